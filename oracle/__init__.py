@@ -1,0 +1,168 @@
+"""CPU oracle for DFA state equivalence (arXiv 2410.22764).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  The GPU library never imports it, and the two
+share no code: the oracle is the plain sequential C in ``oracle.c`` loaded through ctypes.
+
+Each function follows one passage of the paper:
+
+* :func:`moore`      - Alg. sortPR (Sec. 3.3): signature, sort, adjacent difference, scan.
+* :func:`hopcroft`   - Hopcroft's quasi-linear refinement named in Sec. 1.
+* :func:`tablefill`  - pairwise marking, the sequential meaning of Alg. 1 ``trans`` (Sec. 3.1).
+* :func:`closure`    - the per-letter partial transitive closure of Alg. transPR (Sec. 3.4).
+* :func:`canonical`  - canonical relabelling (block id = rank of the block's smallest state).
+* :func:`check_stable` - congruence property check that holds at any size.
+
+All arrays are numpy; ``delta`` is int32 state-major (``delta[s*k+a]``) and ``accept`` is the
+uint32 bitmap (LSB first) of the public contract.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ENOCONVERGE = -3
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc into ``oracle/_build/liboracle.so`` (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
+                        "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32, p = ctypes.c_int32, ctypes.c_void_p
+            lib.oracle_canonical.argtypes = [i32, p, p, p]
+            lib.oracle_moore.argtypes = [i32, i32, p, p, i32, p, p, p]
+            lib.oracle_hopcroft.argtypes = [i32, i32, p, p, p, p]
+            lib.oracle_tablefill.argtypes = [i32, i32, p, p, p, p, p]
+            lib.oracle_closure_levels.argtypes = [i32]
+            lib.oracle_closure_levels.restype = i32
+            lib.oracle_closure.argtypes = [i32, i32, p, p]
+            lib.oracle_check_stable.argtypes = [i32, i32, p, p, p]
+            for f in (lib.oracle_canonical, lib.oracle_moore, lib.oracle_hopcroft,
+                      lib.oracle_tablefill, lib.oracle_closure, lib.oracle_check_stable):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(delta, accept, n, k):
+    delta = np.ascontiguousarray(delta, dtype=np.int32).reshape(-1)
+    accept = np.ascontiguousarray(accept, dtype=np.uint32).reshape(-1)
+    if delta.size != n * k:
+        raise ValueError(f"delta has {delta.size} entries, expected n*k = {n * k}")
+    if accept.size < (n + 31) // 32:
+        raise ValueError("accept bitmap too short")
+    if k == 0:
+        delta = np.zeros(1, np.int32)
+    return delta, accept
+
+
+def canonical(labels) -> tuple[np.ndarray, int]:
+    """Canonical relabelling: id = rank of the block's smallest state. Labels in [0, n)."""
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    n = labels.size
+    out = np.empty(n, np.int32)
+    cnt = ctypes.c_int32(0)
+    rc = _load().oracle_canonical(n, _ptr(labels), _ptr(out), ctypes.byref(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle_canonical failed ({rc})")
+    return out, cnt.value
+
+
+def moore(delta, accept, n: int, k: int, max_passes: int = 0, partial: bool = False):
+    """Moore refinement as Alg. sortPR; returns (block, nblocks, passes).  With ``partial``
+    the partition reached after ``max_passes`` rounds is returned instead of an error."""
+    delta, accept = _prep(delta, accept, n, k)
+    out = np.empty(n, np.int32)
+    nb, ps = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = _load().oracle_moore(n, k, _ptr(delta), _ptr(accept), max_passes, _ptr(out),
+                              ctypes.byref(nb), ctypes.byref(ps))
+    if rc == ENOCONVERGE and not partial:
+        raise RuntimeError(f"oracle_moore hit max_passes={max_passes}")
+    if rc not in (0, ENOCONVERGE):
+        raise ValueError(f"oracle_moore failed ({rc})")
+    return out, nb.value, ps.value
+
+
+def hopcroft(delta, accept, n: int, k: int):
+    """Hopcroft's algorithm; returns (block, nblocks)."""
+    delta, accept = _prep(delta, accept, n, k)
+    out = np.empty(n, np.int32)
+    nb = ctypes.c_int32(0)
+    rc = _load().oracle_hopcroft(n, k, _ptr(delta), _ptr(accept), _ptr(out), ctypes.byref(nb))
+    if rc != 0:
+        raise ValueError(f"oracle_hopcroft failed ({rc})")
+    return out, nb.value
+
+
+def tablefill(delta, accept, n: int, k: int):
+    """Pairwise marking; returns (block, nblocks, rounds) where rounds is the distinguishing
+    depth (length of the longest shortest distinguishing word)."""
+    delta, accept = _prep(delta, accept, n, k)
+    out = np.empty(n, np.int32)
+    nb, rd = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = _load().oracle_tablefill(n, k, _ptr(delta), _ptr(accept), _ptr(out),
+                                  ctypes.byref(nb), ctypes.byref(rd))
+    if rc != 0:
+        raise ValueError(f"oracle_tablefill failed ({rc})")
+    return out, nb.value, rd.value
+
+
+def closure_levels(n: int) -> int:
+    """floor(log2 n) + 1: the number of powers a^(2^i), i = 0..floor(log2 n)."""
+    return int(_load().oracle_closure_levels(n))
+
+
+def closure(delta, n: int, k: int) -> np.ndarray:
+    """Columns of Alg. transPR: out[a*levels + i, q] = delta^T(q, a^(2^i))."""
+    delta = np.ascontiguousarray(delta, dtype=np.int32).reshape(-1)
+    levels = closure_levels(n)
+    out = np.empty((k * levels, n), np.int32)
+    if k == 0:
+        return out
+    rc = _load().oracle_closure(n, k, _ptr(delta), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_closure failed ({rc})")
+    return out
+
+
+def closure_dfa(delta, n: int, k: int) -> tuple[np.ndarray, int]:
+    """The DFA A' of Alg. transPR as a state-major table with k' = k * levels letters."""
+    cols = closure(delta, n, k)
+    return np.ascontiguousarray(cols.T).reshape(-1), cols.shape[0]
+
+
+def check_stable(delta, accept, n: int, k: int, labels) -> bool:
+    """True iff ``labels`` refines {F, Q\\F} and is stable under delta."""
+    delta, accept = _prep(delta, accept, n, k)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    rc = _load().oracle_check_stable(n, k, _ptr(delta), _ptr(accept), _ptr(labels))
+    if rc < 0:
+        raise ValueError(f"oracle_check_stable failed ({rc})")
+    return rc == 1

@@ -1,0 +1,292 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other than itself
+(the definition of state equivalence through delta*, worked examples and closed forms printed
+in arXiv 2410.22764, brute force on tiny inputs, and algebraic invariants)."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_22764_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- definition by words (Sec. 2)
+def _delta_star(delta, k, q, word):
+    # delta*(q, eps) = q ; delta*(q, a w) = delta*(delta(q, a), w)   (Sec. 2)
+    for a in word:
+        q = int(delta[q * k + a])
+    return q
+
+
+def _words_classes(n, k, delta, acc):
+    """p ~ q iff every word w has delta*(p,w) in F <=> delta*(q,w) in F.  Words up to length n
+    suffice: a shortest distinguishing word of an n-state DFA is shorter than n."""
+    words = [w for L in range(n + 1) for w in itertools.product(range(k), repeat=L)]
+    sig = [tuple(bool(acc[_delta_star(delta, k, s, w)]) for w in words) for s in range(n)]
+    first = {}
+    out = []
+    for s in range(n):
+        out.append(first.setdefault(sig[s], len(first)))
+    return np.array(out, np.int32), len(first)
+
+
+def _all_dfas(n, k):
+    for succ in itertools.product(range(n), repeat=n * k):
+        for accmask in range(1 << n):
+            acc = np.array([(accmask >> s) & 1 for s in range(n)], bool)
+            yield np.array(succ, np.int32), acc
+
+
+@pytest.mark.parametrize("n,k", [(1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 1), (3, 2), (4, 1)])
+def test_exhaustive_tiny_against_words_definition(n, k):
+    for delta, acc in _all_dfas(n, k):
+        bits = I.pack_bits(acc)
+        want, wn = _words_classes(n, k, delta, acc)
+        m, mn, _ = oracle.moore(delta, bits, n, k)
+        h, hn = oracle.hopcroft(delta, bits, n, k)
+        t, tn, _ = oracle.tablefill(delta, bits, n, k)
+        assert (m == want).all() and mn == wn
+        assert (h == want).all() and hn == wn
+        assert (t == want).all() and tn == wn
+
+
+def test_random_small_against_words_definition():
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        n = int(rng.integers(1, 7))
+        k = int(rng.integers(0, 3))
+        delta = rng.integers(0, n, n * k).astype(np.int32)
+        acc = rng.random(n) < rng.random()
+        want, wn = _words_classes(n, k, delta, acc)
+        m, mn, _ = oracle.moore(delta, I.pack_bits(acc), n, k)
+        assert (m == want).all() and mn == wn
+
+
+# ---------------------------------------------------------------- three oracles agree
+@pytest.mark.parametrize("p", [0.0, 0.1, 0.5, 0.9, 1.0])
+def test_three_oracles_agree_random(p):
+    for seed in range(40):
+        n = 1 + (seed * 37) % 300
+        k = seed % 5
+        d = I.random_dfa(n, k, p, seed)
+        m, mn, mp = oracle.moore(d.delta, d.accept, n, k)
+        h, hn = oracle.hopcroft(d.delta, d.accept, n, k)
+        t, tn, rounds = oracle.tablefill(d.delta, d.accept, n, k)
+        assert mn == hn == tn
+        assert (m == h).all() and (m == t).all()
+        # Moore's pass count is the distinguishing depth, plus one confirming pass unless the
+        # partition became discrete (the early-exit rule).
+        assert mp == rounds + (1 if mn < n else 0)
+        assert oracle.check_stable(d.delta, d.accept, n, k, m)
+
+
+def test_three_oracles_agree_structured():
+    # mostly-mergeable DFAs: inflated (many equivalent clones) with small alphabets
+    for seed in range(12):
+        d, base = I.inflated_dfa(40 + seed, 1 + seed % 3, 3, 0.5, seed, permute=bool(seed % 2))
+        m, mn, mp = oracle.moore(d.delta, d.accept, d.n, d.k)
+        h, hn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+        t, tn, rounds = oracle.tablefill(d.delta, d.accept, d.n, d.k)
+        assert mn == hn == tn and (m == h).all() and (m == t).all()
+        assert mp == rounds + (1 if mn < d.n else 0)
+
+
+def test_canonical_labels_are_first_occurrence():
+    lab = np.array([5, 5, 2, 7, 2, 0, 7, 1], np.int32)
+    out, c = oracle.canonical(lab)
+    assert out.tolist() == [0, 0, 1, 2, 1, 3, 2, 4] and c == 5
+
+
+def test_planted_mistake_is_caught():
+    """A labelling that merges two inequivalent states must fail the stability check."""
+    d = I.fig1_dfa()
+    b, _ = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    bad = b.copy()
+    bad[1] = bad[0]  # q0 and q1 are apart by a^8 (Sec. 3.4)
+    assert oracle.check_stable(d.delta, d.accept, d.n, d.k, b)
+    assert not oracle.check_stable(d.delta, d.accept, d.n, d.k, bad)
+
+
+# ---------------------------------------------------------------- closed forms and examples
+def test_fig1_path_needs_eight_rounds_and_closure_separates_q0_q1_in_one():
+    # Fig. 1: accepts a^j with j > 8; every partition refinement needs 8 iterations to split
+    # q0 from q1, while with the closure the letter a^8 splits them in the first iteration.
+    d = I.fig1_dfa()
+    b, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    assert nb == 10 and ps == 8
+    dc, kc = oracle.closure_dfa(d.delta, d.n, d.k)
+    assert kc == 4  # a, a^2, a^4, a^8 (floor(log2 10) = 3)
+    one, _, _ = oracle.moore(dc, d.accept, d.n, kc, max_passes=1, partial=True)
+    assert one[0] != one[1]
+    plain_one, _, _ = oracle.moore(d.delta, d.accept, d.n, d.k, max_passes=1, partial=True)
+    assert plain_one[0] == plain_one[1]
+    bc, nbc, psc = oracle.moore(dc, d.accept, d.n, kc)
+    assert nbc == 10 and (bc == b).all() and psc < ps
+
+
+def _read_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_fig2_bitsplitter_b3_matches_figure():
+    d = I.bitsplitter_dfa(3)
+    assert d.n == 8 and d.k == 2
+    rows = _read_golden("fig2_b3.txt")
+    acc = d.accepting()
+    for r in rows:
+        if r[0] == "edge":
+            src, letter, dst = int(r[1], 2), int(r[2][1:]) - 1, int(r[3], 2)
+            assert d.delta[src * d.k + letter] == dst, r
+        else:
+            assert acc[int(r[1], 2)]
+    assert acc.sum() == sum(1 for r in rows if r[0] == "accept")
+    assert sum(1 for r in rows if r[0] == "edge") == d.n * d.k
+
+
+def test_fig2_fib5_matches_figure():
+    d = I.cyclic_fib_dfa(5)
+    rows = _read_golden("fig2_fib5.txt")
+    assert d.n == 8
+    for r in rows:
+        if r[0] == "edge":
+            assert d.delta[int(r[1])] == int(r[2])
+    assert sorted(np.nonzero(d.accepting())[0].tolist()) == [int(r[1]) for r in rows
+                                                             if r[0] == "accept"]
+
+
+def test_fibonacci_words_match_listing():
+    for idx, word in _read_golden("fibonacci_words.txt"):
+        assert "".join(map(str, I.fibonacci_word_n(int(idx)))) == word
+    inf = I.fibonacci_word(200)
+    for i in range(1, 12):
+        w = I.fibonacci_word_n(i)
+        assert (inf[: w.size] == w).all()
+
+
+@pytest.mark.parametrize("i", range(2, 16))
+def test_cyclic_fibonacci_classes_and_rounds(i):
+    # Table 2: size output = N; Sec. 4.2: n-2 parallel iterations on Fib automata
+    d = I.cyclic_fib_dfa(i)
+    b, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    h, hn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    assert nb == d.n == hn and (b == h).all()
+    assert ps == max(d.n - 2, 0)
+
+
+@pytest.mark.parametrize("nbits", range(1, 13))
+def test_bitsplitter_classes_and_rounds(nbits):
+    # Table 2: B_n has size output 2^n and takes n-1 iterations
+    d = I.bitsplitter_dfa(nbits)
+    b, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    h, hn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    assert nb == hn == 1 << nbits and (b == h).all()
+    assert ps == nbits - 1
+
+
+def test_table2_bitsplitter_rows_small():
+    for name, N, sig, size_out, iters in _read_golden("table2_rows.txt"):
+        if not name.startswith("B") or int(name[1:]) > 16:
+            continue
+        d = I.bitsplitter_dfa(int(name[1:]))
+        assert d.n == int(N) and d.k == int(sig)
+        _, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+        assert nb == int(size_out) and ps == int(iters)
+
+
+def test_table2_fibonacci_sizes():
+    # the table's Fib_i has N = |w_{i+1}| states and is minimal (size output = N)
+    for name, N, sig, size_out, iters in _read_golden("table2_rows.txt"):
+        if not name.startswith("Fib"):
+            continue
+        i = int(name[3:])
+        assert I.fibonacci_word_n(i + 1).size == int(N) == int(size_out)
+        # iterations column: one confirming pass after the n-2 splitting rounds
+        assert int(iters) == int(N) - 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 10, 33, 100, 257, 1000, 2048])
+def test_path_fibonacci_closed_form(n):
+    d = I.path_fib_dfa(n)
+    w = I.fibonacci_word(n)
+    want = n - (1 if n >= 2 and w[n - 2] == w[n - 1] else 0)
+    b, nb, _ = oracle.moore(d.delta, d.accept, d.n, d.k)
+    h, hn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    assert nb == hn == want and (b == h).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_inflated_classes_equal_base_classes(seed):
+    m, k, c = 300 + 50 * seed, 1 + seed % 4, 2 + seed
+    d, base = I.inflated_dfa(m, k, c, 0.5, seed, permute=seed % 2 == 0)
+    bb, bn = oracle.hopcroft(base.delta, base.accept, m, k)
+    b, nb = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    assert nb == bn
+    # every clone sits in the block of its base state
+    raw = np.arange(d.n)
+    ident = I.seeded_permutation(d.n, seed) if seed % 2 == 0 else raw
+    lab = np.empty(d.n, np.int64)
+    lab[ident] = bb[raw // c]
+    canon, cn = oracle.canonical(lab.astype(np.int32))
+    assert cn == bn and (canon == b).all()
+
+
+def test_uniform_acceptance_gives_one_block():
+    for k in range(0, 4):
+        for p in (0.0, 1.0):
+            d = I.random_dfa(500, k, p, 3)
+            b, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+            assert nb == 1 and (b == 0).all() and ps == 1
+
+
+# ---------------------------------------------------------------- closure (Alg. transPR)
+def test_closure_columns_are_powers_of_delta():
+    for seed in range(5):
+        n, k = 50 + 31 * seed, 1 + seed % 3
+        d = I.random_dfa(n, k, 0.5, seed)
+        cols = oracle.closure(d.delta, n, k)
+        levels = oracle.closure_levels(n)
+        assert levels == int(np.floor(np.log2(n))) + 1
+        for a in range(k):
+            for i in range(levels):
+                for q in range(0, n, 7):
+                    t = q
+                    for _ in range(1 << i):
+                        t = int(d.delta[t * k + a])
+                    assert cols[a * levels + i, q] == t
+
+
+@pytest.mark.parametrize("maker", ["path", "cyclic", "bits", "random", "inflated"])
+def test_closure_preserves_equivalence(maker):
+    if maker == "path":
+        d = I.path_fib_dfa(777)
+    elif maker == "cyclic":
+        d = I.cyclic_fib_dfa(12)
+    elif maker == "bits":
+        d = I.bitsplitter_dfa(9)
+    elif maker == "random":
+        d = I.random_dfa(900, 3, 0.4, 11)
+    else:
+        d, _ = I.inflated_dfa(200, 2, 4, 0.5, 5)
+    b, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    dc, kc = oracle.closure_dfa(d.delta, d.n, d.k)
+    bc, nbc, psc = oracle.moore(dc, d.accept, d.n, kc)
+    assert nbc == nb and (bc == b).all()
+    assert psc <= ps
+
+
+def test_moore_cap_reports_nonconvergence():
+    d = I.cyclic_fib_dfa(10)
+    with pytest.raises(RuntimeError):
+        oracle.moore(d.delta, d.accept, d.n, d.k, max_passes=5)
+
+
+def test_bad_delta_rejected():
+    delta = np.array([0, 5], np.int32)
+    with pytest.raises(ValueError):
+        oracle.moore(delta, I.pack_bits(np.array([1, 0], bool)), 2, 1)
+    with pytest.raises(ValueError):
+        oracle.hopcroft(delta, I.pack_bits(np.array([1, 0], bool)), 2, 1)
