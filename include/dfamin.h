@@ -1,0 +1,123 @@
+/*
+ * dfamin: GB300 (sm_103a) DFA minimizer - public C ABI.
+ *
+ * Computes the coarsest partition of the states of a complete DFA that refines {F, Q\F} and is
+ * stable under the transition function, i.e. language equivalence of states (arXiv 2410.22764,
+ * Sec. 2 problem statement and Definition of a DFA).  The initial state is not an input and
+ * unreachable states are not removed: every state is classified (Sec. 2, "we assume that all
+ * the states in a DFA are reachable").  The method is signature-based partition refinement
+ * (Alg. sortPR, Sec. 3.3), optionally on the partial transitive closure A' of Alg. transPR
+ * (Sec. 3.4), which has the same state equivalence as A.
+ *
+ * Data conventions (all calls):
+ *   n       number of states, 1 <= n < 2^31.  States are 0..n-1.
+ *   k       number of letters, k >= 0.  Letters are 0..k-1.  n*k < 2^40.
+ *   delta   int32 [n*k], STATE-MAJOR: delta[s*k + a] = delta(s, a), each in [0, n).  (The paper
+ *           stores delta[a][q] letter-major, Sec. 2 "Representation"; the library may use any
+ *           layout internally.)  May be NULL when k == 0.
+ *   accept  uint32 bitmap [(n+31)/32]: state s is accepting iff (accept[s>>5] >> (s&31)) & 1.
+ *   out_block int32 [n]: canonical block ids.  The id of a block is the number of blocks whose
+ *           smallest state is smaller than its own smallest state (first-occurrence order over
+ *           s = 0..n-1), so block ids are 0..nblocks-1 and out_block[0] == 0.
+ *
+ * Memory and streams: every array pointer is a DEVICE pointer (cudaMalloc / torch CUDA memory)
+ * owned by the caller.  Calls are asynchronous on `stream` (NULL = legacy default stream): they
+ * validate host-side arguments, enqueue work and return.  Outputs are valid once the stream has
+ * reached that point.  The inputs are never modified.  Nothing here synchronises the stream.
+ *
+ * Errors: host-detectable errors (bad sizes, NULL pointers, workspace too small, launch
+ * failure) are returned synchronously and nothing is enqueued.  Errors found on the device
+ * (a delta entry out of range, a bounded wait that ran out, no convergence within max_passes)
+ * are written to the `status` output (DFAMIN_OK when fine); in that case out_block is not
+ * meaningful and *nblocks is set to minus the status code.
+ */
+#ifndef DFAMIN_H
+#define DFAMIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same handle as cudaStream_t; declared opaquely so this header needs no CUDA headers. */
+typedef struct CUstream_st *dfamin_stream_t;
+
+typedef enum {
+    DFAMIN_OK = 0,
+    DFAMIN_EINVAL = 1,      /* bad argument, or (on device) a delta entry outside [0, n) */
+    DFAMIN_ENOMEM = 2,      /* workspace too small / internal allocation failed */
+    DFAMIN_ECUDA = 3,       /* a CUDA runtime call failed */
+    DFAMIN_ETIMEOUT = 4,    /* a bounded device-side wait (CTA barrier) ran out */
+    DFAMIN_ENOCONVERGE = 5, /* max_passes reached before the partition was stable */
+    DFAMIN_EPROBE = 6       /* hash-table probe sequence exhausted (table full) */
+} dfamin_status;
+
+/* closure */
+#define DFAMIN_CLOSURE_OFF 0   /* plain refinement on A (Alg. sortPR semantics) */
+#define DFAMIN_CLOSURE_ON 1    /* refinement on the closed DFA A' of Alg. transPR */
+
+/* flags */
+#define DFAMIN_FLAG_KEEP_IDENTITY 1u  /* closure: also close letters whose delta is the identity
+                                         (by default their columns, all equal to the identity,
+                                         are left out; this changes no partition and no pass) */
+#define DFAMIN_FLAG_HASH_BLOCK_ONLY 2u /* testing: hash only the old block id (forces collisions
+                                         that the full-tuple check must resolve) */
+#define DFAMIN_FLAG_HASH_CONSTANT 4u   /* testing: constant hash (every group collides) */
+
+typedef struct {
+    int32_t closure;     /* DFAMIN_CLOSURE_OFF or DFAMIN_CLOSURE_ON */
+    int32_t max_passes;  /* cap on signature passes; 0 = n + 1 */
+    uint32_t flags;      /* DFAMIN_FLAG_* */
+    int32_t ctas;        /* 0 = automatic; otherwise number of CTAs for one DFA (tuning) */
+    int32_t smem_states; /* 0 = automatic; largest n solved by one CTA in shared memory */
+    int32_t reserved[3]; /* must be 0 */
+} dfamin_options;
+
+/* Fills *opt with the defaults (closure off, automatic tuning). */
+void dfamin_default_options(dfamin_options *opt);
+
+/*
+ * dfamin_minimize - minimize one DFA (Sec. 2 problem; Alg. sortPR refinement, Sec. 3.3).
+ * nblocks: device int32 scalar, receives the number of blocks (or -status on a device error).
+ * Uses a workspace owned by the library (one per device and stream, grown on demand with
+ * cudaMalloc, which may synchronise the device when it grows).  Closure off.
+ */
+dfamin_status dfamin_minimize(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,
+                              int32_t *out_block, int32_t *nblocks, dfamin_stream_t stream);
+
+/*
+ * dfamin_workspace_size - bytes of device workspace dfamin_minimize_ex needs for (n, k, opt).
+ */
+dfamin_status dfamin_workspace_size(int32_t n, int32_t k, const dfamin_options *opt,
+                                    size_t *bytes);
+
+/*
+ * dfamin_minimize_ex - as dfamin_minimize, with options and a caller-owned workspace.
+ *   opt        NULL = defaults.  closure = ON runs the refinement on A' (Alg. transPR,
+ *              Sec. 3.4): columns delta^T(., a^(2^i)) for i = 1..floor(log2 n) are built by
+ *              pointer doubling and appended to every state's signature.
+ *   workspace  device memory of at least dfamin_workspace_size() bytes, 256-byte aligned,
+ *              any contents; the call owns it until the stream passes the call.  Calls that
+ *              overlap on the GPU must not share a workspace.
+ *   passes     device int32 scalar or NULL: number of signature passes executed.  A pass is
+ *              one refinement round; the loop stops after a pass that left the block count
+ *              unchanged, or once every block is a singleton (0 passes if {F, Q\F} is already
+ *              discrete).
+ *   status     device int32 scalar or NULL: DFAMIN_OK or the device-detected error.
+ */
+dfamin_status dfamin_minimize_ex(int32_t n, int32_t k, const int32_t *delta,
+                                 const uint32_t *accept, int32_t *out_block, int32_t *nblocks,
+                                 const dfamin_options *opt, void *workspace,
+                                 size_t workspace_bytes, int32_t *passes, int32_t *status,
+                                 dfamin_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char *dfamin_status_string(dfamin_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFAMIN_H */

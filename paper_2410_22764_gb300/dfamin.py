@@ -1,0 +1,195 @@
+"""Thin Python binding of the dfamin C ABI (``include/dfamin.h``).
+
+Argument marshalling only: every step of the minimization runs in the CUDA library
+``libdfamin.so`` built from ``csrc/``.  PyTorch supplies device memory and streams.  There is no
+CPU fallback: importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfamin.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONVERGE, EPROBE = range(7)
+CLOSURE_OFF, CLOSURE_ON = 0, 1
+FLAG_KEEP_IDENTITY = 1
+FLAG_HASH_BLOCK_ONLY = 2
+FLAG_HASH_CONSTANT = 4
+
+# names declared in include/dfamin.h (checked against the library's exports by the tests)
+ABI_FUNCTIONS = (
+    "dfamin_default_options",
+    "dfamin_minimize",
+    "dfamin_workspace_size",
+    "dfamin_minimize_ex",
+    "dfamin_status_string",
+)
+
+
+class DfaminError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("closure", ctypes.c_int32), ("max_passes", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("ctas", ctypes.c_int32),
+                ("smem_states", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, u32, p, sz = ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+    lib.dfamin_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.dfamin_default_options.restype = None
+    lib.dfamin_minimize.argtypes = [i32, i32, p, p, p, p, p]
+    lib.dfamin_workspace_size.argtypes = [i32, i32, ctypes.POINTER(Options),
+                                          ctypes.POINTER(sz)]
+    lib.dfamin_minimize_ex.argtypes = [i32, i32, p, p, p, p, ctypes.POINTER(Options), p, sz,
+                                       p, p, p]
+    lib.dfamin_status_string.argtypes = [ctypes.c_int]
+    lib.dfamin_status_string.restype = ctypes.c_char_p
+    for f in (lib.dfamin_minimize, lib.dfamin_workspace_size, lib.dfamin_minimize_ex):
+        f.restype = ctypes.c_int
+    del u32
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return _lib.dfamin_status_string(int(code)).decode()
+
+
+def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: int = 0,
+            smem_states: int = 0) -> Options:
+    o = Options()
+    _lib.dfamin_default_options(ctypes.byref(o))
+    o.closure = CLOSURE_ON if closure else CLOSURE_OFF
+    o.max_passes, o.flags, o.ctas, o.smem_states = max_passes, flags, ctas, smem_states
+    return o
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def workspace_size(n: int, k: int, opt: Options | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    rc = _lib.dfamin_workspace_size(n, k, ctypes.byref(opt or options()), ctypes.byref(out))
+    if rc:
+        raise DfaminError(rc, "dfamin_workspace_size")
+    return out.value
+
+
+@dataclass
+class Result:
+    """Device-side outputs of one call (valid once the stream has passed the call)."""
+    out_block: torch.Tensor  # int32 [n]
+    scalars: torch.Tensor    # int32 [3] = nblocks, passes, status
+
+    def host(self):
+        s = self.scalars.cpu().tolist()
+        return self.out_block.cpu().numpy(), s[0], s[1], s[2]
+
+
+class Workspace:
+    """Caller-owned device workspace (torch memory) for dfamin_minimize_ex."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(256, (nbytes + 255) // 256 * 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def minimize_ex(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
+                opt: Options | None = None, workspace: Workspace | None = None,
+                out_block: torch.Tensor | None = None, scalars: torch.Tensor | None = None,
+                stream=None) -> Result:
+    """Enqueue dfamin_minimize_ex on ``stream``; returns device tensors (no synchronisation).
+
+    ``delta`` int32 [n*k] state-major and ``accept`` a 32-bit bitmap [(n+31)//32] (int32 or
+    uint32 storage) must be CUDA tensors.
+    """
+    opt = opt or options()
+    dev = delta.device if k > 0 else accept.device
+    if dev.type != "cuda" or accept.device.type != "cuda":
+        raise ValueError("delta and accept must be CUDA tensors")
+    if k > 0 and (delta.dtype != torch.int32 or delta.numel() != n * k
+                  or not delta.is_contiguous()):
+        raise ValueError("delta must be a contiguous int32 tensor of n*k entries")
+    if accept.element_size() != 4 or accept.numel() < (n + 31) // 32:
+        raise ValueError("accept must be a 32-bit bitmap of (n+31)//32 words")
+    ws = (workspace or Workspace(dev)).get(workspace_size(n, k, opt))
+    if out_block is None:
+        out_block = torch.empty(n, dtype=torch.int32, device=dev)
+    if scalars is None:
+        scalars = torch.zeros(3, dtype=torch.int32, device=dev)
+    sp = scalars.data_ptr()
+    rc = _lib.dfamin_minimize_ex(
+        n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0), _ptr(accept), _ptr(out_block),
+        ctypes.c_void_p(sp), ctypes.byref(opt), _ptr(ws), ctypes.c_size_t(ws.numel()),
+        ctypes.c_void_p(sp + 4), ctypes.c_void_p(sp + 8), _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize_ex")
+    return Result(out_block, scalars)
+
+
+def minimize(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
+             out_block: torch.Tensor | None = None, nblocks: torch.Tensor | None = None,
+             stream=None):
+    """Enqueue dfamin_minimize (library-owned workspace); returns (out_block, nblocks)."""
+    dev = accept.device
+    if out_block is None:
+        out_block = torch.empty(n, dtype=torch.int32, device=dev)
+    if nblocks is None:
+        nblocks = torch.zeros(1, dtype=torch.int32, device=dev)
+    rc = _lib.dfamin_minimize(n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0),
+                              _ptr(accept), _ptr(out_block), _ptr(nblocks),
+                              _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize")
+    return out_block, nblocks
+
+
+def to_device(delta: np.ndarray, accept: np.ndarray, device="cuda"):
+    """Copy a host DFA (numpy int32 delta, uint32 bitmap) to CUDA tensors."""
+    d = torch.from_numpy(np.ascontiguousarray(delta, dtype=np.int32)).to(device)
+    a = torch.from_numpy(np.ascontiguousarray(accept, dtype=np.uint32).view(np.int32)).to(device)
+    return d, a
+
+
+def minimize_host(n: int, k: int, delta: np.ndarray, accept: np.ndarray, *,
+                  closure: bool = False, flags: int = 0, max_passes: int = 0,
+                  device="cuda"):
+    """Convenience end-to-end call on host arrays; returns (block, nblocks, passes, status)."""
+    d, a = to_device(delta, accept, device)
+    r = minimize_ex(n, k, d, a, opt=options(closure=closure, flags=flags,
+                                            max_passes=max_passes))
+    return r.host()
