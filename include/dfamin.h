@@ -113,6 +113,10 @@ dfamin_status dfamin_minimize_ex(int32_t n, int32_t k, const int32_t *delta,
                                  size_t workspace_bytes, int32_t *passes, int32_t *status,
                                  dfamin_stream_t stream);
 
+/* Text of the last CUDA runtime failure seen by the library on the calling thread ("" if
+ * none); meant for diagnostics after DFAMIN_ECUDA / DFAMIN_ENOMEM.  Thread-local storage. */
+const char *dfamin_last_cuda_error(void);
+
 /* Human-readable name of a status code (static string). */
 const char *dfamin_status_string(dfamin_status s);
 

@@ -32,6 +32,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <map>
@@ -719,25 +720,43 @@ struct DeviceInfo {
 std::mutex g_mu;
 std::map<int, DeviceInfo> g_dev;
 
+// Last CUDA failure seen by this thread (dfamin_last_cuda_error).
+thread_local char g_last_error[256] = "";
+
+bool cuda_ok(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return true;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", what, cudaGetErrorString(e),
+             (int)e);
+    return false;
+}
+
 dfamin_status device_info(DeviceInfo* out)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DFAMIN_ECUDA;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_dev.find(dev);
     if (it != g_dev.end()) { *out = it->second; return DFAMIN_OK; }
     DeviceInfo d;
     int v = 0;
-    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    if (!cuda_ok(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev),
+                 "cudaDeviceGetAttribute(SMs)"))
         return DFAMIN_ECUDA;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    if (!cuda_ok(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                 "cudaDeviceGetAttribute(smem)"))
         return DFAMIN_ECUDA;
-    d.smem_optin = (size_t)v;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.team_blocks_per_sm, team_kernel,
-                                                      kThreads, 0) != cudaSuccess)
+    cudaFuncAttributes fa;
+    if (!cuda_ok(cudaFuncGetAttributes(&fa, small_kernel), "cudaFuncGetAttributes"))
         return DFAMIN_ECUDA;
-    if (cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)d.smem_optin) != cudaSuccess)
+    d.smem_optin = (size_t)v > fa.sharedSizeBytes ? (size_t)v - fa.sharedSizeBytes : 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.team_blocks_per_sm,
+                                                               team_kernel, kThreads, 0),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
+        return DFAMIN_ECUDA;
+    if (!cuda_ok(cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)d.smem_optin),
+                 "cudaFuncSetAttribute(small_kernel)"))
         return DFAMIN_ECUDA;
     g_dev[dev] = d;
     *out = d;
@@ -792,7 +811,8 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.flags = o.flags;
     J.timeout_ns = kBarrierTimeoutNs;
 
-    if (cudaMemsetAsync(base + L.ctrl, 0, L.zero_end - L.ctrl, stream) != cudaSuccess)
+    if (!cuda_ok(cudaMemsetAsync(base + L.ctrl, 0, L.zero_end - L.ctrl, stream),
+                 "cudaMemsetAsync(ctrl)"))
         return DFAMIN_ECUDA;
 
     const int small_limit = o.smem_states > 0 ? o.smem_states : 4096;
@@ -800,7 +820,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     const size_t smem = small_smem_bytes(n, &scap);
     if (n <= small_limit && n <= kSmallMaxStates && smem <= di.smem_optin) {
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
-        return cudaGetLastError() == cudaSuccess ? DFAMIN_OK : DFAMIN_ECUDA;
+        return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
     }
     int max_ctas = di.sms * di.team_blocks_per_sm;
     if (max_ctas > kMaxCtas) max_ctas = kMaxCtas;
@@ -810,8 +830,9 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     if (o.ctas == 0 && want < ctas) ctas = (int)(want > 0 ? want : 1);
     if (ctas > max_ctas) ctas = max_ctas;
     void* args[] = {&J};
-    if (cudaLaunchCooperativeKernel((const void*)team_kernel, dim3(ctas), dim3(kThreads), args, 0,
-                                    stream) != cudaSuccess)
+    if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)team_kernel, dim3(ctas),
+                                             dim3(kThreads), args, 0, stream),
+                 "team_kernel cooperative launch"))
         return DFAMIN_ECUDA;
     return DFAMIN_OK;
 }
@@ -868,19 +889,20 @@ DFAMIN_API dfamin_status dfamin_minimize(int32_t n, int32_t k, const int32_t* de
     dfamin_default_options(&o);
     const size_t need = make_layout(n, k, o).total;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DFAMIN_ECUDA;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
     void* ws = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         OwnedWs& w = g_ws[std::make_pair(dev, (cudaStream_t)stream)];
         if (w.bytes < need) {
             if (w.ptr) {
-                if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DFAMIN_ECUDA;
+                if (!cuda_ok(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize"))
+                    return DFAMIN_ECUDA;
                 cudaFree(w.ptr);
                 w.ptr = nullptr;
                 w.bytes = 0;
             }
-            if (cudaMalloc(&w.ptr, need) != cudaSuccess) return DFAMIN_ENOMEM;
+            if (!cuda_ok(cudaMalloc(&w.ptr, need), "cudaMalloc(workspace)")) return DFAMIN_ENOMEM;
             w.bytes = need;
         }
         ws = w.ptr;
@@ -888,6 +910,8 @@ DFAMIN_API dfamin_status dfamin_minimize(int32_t n, int32_t k, const int32_t* de
     return launch_one(n, k, delta, accept, out_block, nblocks, o, ws, need, nullptr, nullptr,
                       (cudaStream_t)stream);
 }
+
+DFAMIN_API const char* dfamin_last_cuda_error(void) { return g_last_error; }
 
 DFAMIN_API const char* dfamin_status_string(dfamin_status s)
 {

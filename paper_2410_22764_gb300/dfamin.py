@@ -29,12 +29,16 @@ ABI_FUNCTIONS = (
     "dfamin_workspace_size",
     "dfamin_minimize_ex",
     "dfamin_status_string",
+    "dfamin_last_cuda_error",
 )
 
 
 class DfaminError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {status_string(code)} ({code})")
+        detail = ""
+        if code in (ECUDA, ENOMEM):
+            detail = " [" + _lib.dfamin_last_cuda_error().decode() + "]"
+        super().__init__(f"{what}: {status_string(code)} ({code}){detail}")
         self.code = code
 
 
@@ -59,6 +63,8 @@ def _load():
                                        p, p, p]
     lib.dfamin_status_string.argtypes = [ctypes.c_int]
     lib.dfamin_status_string.restype = ctypes.c_char_p
+    lib.dfamin_last_cuda_error.argtypes = []
+    lib.dfamin_last_cuda_error.restype = ctypes.c_char_p
     for f in (lib.dfamin_minimize, lib.dfamin_workspace_size, lib.dfamin_minimize_ex):
         f.restype = ctypes.c_int
     del u32

@@ -290,3 +290,32 @@ def test_bad_delta_rejected():
         oracle.moore(delta, I.pack_bits(np.array([1, 0], bool)), 2, 1)
     with pytest.raises(ValueError):
         oracle.hopcroft(delta, I.pack_bits(np.array([1, 0], bool)), 2, 1)
+
+
+# ---------------------------------------------------------------- path distinguishing depth
+def _path_dfa_from_word(w):
+    n = w.size
+    i = np.arange(n)
+    delta = np.stack([np.minimum(i + 1, n - 1), i], 1).astype(np.int32).reshape(-1)
+    return delta, I.pack_bits(w.astype(bool))
+
+
+def test_path_depth_matches_moore_and_tablefill():
+    from oracle.path_depth import path_depth, path_passes
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        n = int(rng.integers(1, 80))
+        w = (rng.random(n) < rng.random()).astype(np.uint8)
+        delta, acc = _path_dfa_from_word(w)
+        _, nb, ps = oracle.moore(delta, acc, n, 2)
+        _, tn, rounds = oracle.tablefill(delta, acc, n, 2)
+        assert path_passes(w) == (ps, nb)
+        assert path_depth(w) == (rounds, tn)
+
+
+@pytest.mark.parametrize("n", [2, 7, 100, 1000, 4096])
+def test_path_depth_fibonacci(n):
+    from oracle.path_depth import path_passes
+    d = I.path_fib_dfa(n)
+    _, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    assert path_passes(I.fibonacci_word(n)) == (ps, nb)
