@@ -10,7 +10,7 @@
  * (Sec. 3.4), which has the same state equivalence as A.
  *
  * Data conventions (all calls):
- *   n       number of states, 1 <= n < 2^31.  States are 0..n-1.
+ *   n       number of states, 1 <= n <= 2^30.  States are 0..n-1.
  *   k       number of letters, k >= 0.  Letters are 0..k-1.  n*k < 2^40.
  *   delta   int32 [n*k], STATE-MAJOR: delta[s*k + a] = delta(s, a), each in [0, n).  (The paper
  *           stores delta[a][q] letter-major, Sec. 2 "Representation"; the library may use any
@@ -65,6 +65,15 @@ typedef enum {
 #define DFAMIN_FLAG_HASH_BLOCK_ONLY 2u /* testing: hash only the old block id (forces collisions
                                          that the full-tuple check must resolve) */
 #define DFAMIN_FLAG_HASH_CONSTANT 4u   /* testing: constant hash (every group collides) */
+#define DFAMIN_FLAG_TRACE 8u           /* record per-phase device timestamps (see below) */
+
+/* Phase trace.  With DFAMIN_FLAG_TRACE the workspace grows by DFAMIN_TRACE_BYTES, and the last
+ * DFAMIN_TRACE_BYTES of the required workspace receive int64 values: [0] = number of records,
+ * then records (tag, t_ns) with tag = (pass << 8) | phase and t_ns the device global timer
+ * when the phase ended.  Phases: 0 start, 1 validation, 2 initial partition, 3 one closure
+ * level, 4 leaders' signatures, 5 members' regrouping, 6 moves applied, 7 leader count,
+ * 8 canonical ids written.  Records beyond capacity are counted but not stored. */
+#define DFAMIN_TRACE_BYTES 262144
 
 typedef struct {
     int32_t closure;     /* DFAMIN_CLOSURE_OFF or DFAMIN_CLOSURE_ON */

@@ -45,10 +45,21 @@
 
 namespace {
 
-constexpr int kThreads = 256;             // threads per CTA (team and small kernels)
+constexpr int kThreads = 256;             // threads per CTA of the one-CTA kernel
+#ifndef DFAMIN_TEAM_THREADS
+#define DFAMIN_TEAM_THREADS 256           // threads per CTA of the team kernel
+#endif
+#ifndef DFAMIN_TEAM_MIN_CTAS
+#define DFAMIN_TEAM_MIN_CTAS 4            // team kernel: CTAs per SM the register budget targets
+#endif
+#ifndef DFAMIN_PREFETCH
+#define DFAMIN_PREFETCH 1                 // load the next state's block id and row ahead
+#endif
+#ifndef DFAMIN_SLOT_CACHE
+#define DFAMIN_SLOT_CACHE 512             // per-CTA group-cache entries (rows of <= 8 ints)
+#endif
+constexpr int kTeamThreads = DFAMIN_TEAM_THREADS;
 constexpr int kMaxCtas = 8192;            // capacity of the per-CTA count array
-constexpr uint32_t kEpochBits = 20;       // table epoch field width
-constexpr uint32_t kEpochPeriod = (1u << kEpochBits) - 1;  // epochs 1..period, 0 = empty
 constexpr int64_t kBarrierTimeoutNs = 4000000000ll;        // 4 s per CTA barrier
 constexpr int kSmallMaxStates = 8192;     // largest n for the shared-memory kernel
 
@@ -62,7 +73,8 @@ struct Ctrl {                      // zeroed by the host before every launch
     int min_f_rev;                 // n - (smallest accepting state), 0 if none
     int min_n_rev;                 // n - (smallest rejecting state), 0 if none
     int ncl_letters;               // letters that get closure columns
-    int pad[8];
+    int nlead;                     // entries in the global leader list
+    int pad[7];
 };
 
 struct Job {
@@ -77,9 +89,15 @@ struct Job {
     int32_t* cl;                         // closure columns [ncl_letters*(levels-1)][n]
     int32_t* cl_letter;                  // [k] letters with closure columns (compacted)
     int32_t* nonid;                      // [k] 1 if letter is not the identity
-    uint64_t* table;                     // [mask+1]
+    uint32_t* table;                     // [mask+1] group slots (smallest state), kEmpty
+    int32_t* sig;                        // [n * sig_stride] signature rows
+    int32_t sig_stride;                  // ints per row, multiple of 4, >= ncols + 1
     int32_t* lst_s;                      // [n] changed states, per-CTA segments
-    uint32_t* lst_slot;                  // [n] their table slots
+    uint32_t* lst_slot;                  // [n] their table slots (or kCached | cache index)
+    uint32_t* lst_rst;                   // [n] slots to empty next round, per-CTA segments
+    int32_t* lead;                       // [n] global leader list (append-only)
+    uint32_t* lead_slot;                 // [n] table slot of each listed leader's group
+    int32_t* stg;                        // [n] per-CTA staging of new leaders
     int32_t* cta_cnt;                    // [kMaxCtas]
     Ctrl* ctrl;
     uint32_t mask;                       // table capacity - 1
@@ -87,6 +105,8 @@ struct Job {
     int32_t max_passes;
     uint32_t flags;
     int64_t timeout_ns;
+    long long* trace;                    // phase trace or null
+    long long trace_cap;                 // records
 };
 
 __device__ __forceinline__ uint64_t gtimer()
@@ -103,16 +123,23 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
 __device__ __forceinline__ void set_status(Ctrl* c, int code) { atomicCAS(&c->status, 0, code); }
+
+// One trace record (written by one thread only).
+__device__ __forceinline__ void trace_mark(const Job& J, bool writer, int pass, int phase)
+{
+    if (J.trace && writer) {
+        const long long i = J.trace[0];
+        if (i < J.trace_cap) {
+            J.trace[1 + 2 * i] = ((long long)pass << 8) | phase;
+            J.trace[2 + 2 * i] = (long long)gtimer();
+        }
+        J.trace[0] = i + 1;
+    }
+}
 
 // splitmix64 finalizer (Steele, Lea & Flood 2014); the hash only steers the table probe.
 __device__ __forceinline__ uint64_t fmix64(uint64_t z)
@@ -161,7 +188,7 @@ struct TeamSync {
     int64_t timeout_ns;
 };
 
-__device__ bool team_barrier(TeamSync& ts)
+__device__ __forceinline__ bool team_barrier(TeamSync& ts)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -246,56 +273,475 @@ __device__ int cta_min(int v)
 }
 
 // ------------------------------------------------------------------------------------------
-// Global hash table (team kernel).  Slot word: [epoch:20 | hash:12 | state:32]; a slot whose
-// epoch differs from the round's epoch is empty.  All members of one group end in the same slot
-// (a slot, once claimed in a round, never changes owner group) and its low word converges to
-// the group's smallest state by atomicMin (the high word is equal for the whole group).
+// Signature rows.  sig[s*SS .. s*SS+SS) holds the full signature of s in the current round,
+// T(s) = (block[s], block[succ(s,0)], ..., block[succ(s,K-1)]), padded with zeros to SS ints
+// (SS a multiple of 4, so rows are read and written as int4).  A leader writes its row in phase
+// A; a member compares its own signature with its leader's row (one sector instead of
+// regathering the leader's successors); a member that differs publishes its row before it
+// enters the hash table, so the table can verify equality against any slot holder's row.
 // ------------------------------------------------------------------------------------------
-__device__ bool tuples_equal(const Job& J, int s, int t, int leader, int ncols)
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr uint32_t kFail = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
 {
-    if (__ldcg(&J.block[t]) != leader) return false;
-    for (int c = 0; c < ncols; ++c) {
-        const int bs = __ldcg(&J.block[succ_col(J, s, c)]);
-        const int bt = __ldcg(&J.block[succ_col(J, t, c)]);
-        if (bs != bt) return false;
-    }
-    return true;
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Returns the slot of s's group, or UINT32_MAX after setting DFAMIN_EPROBE.
-__device__ uint32_t table_insert(const Job& J, int s, int leader, uint64_t h, uint32_t epoch,
-                                 int ncols, int* s_claims)
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p)
 {
-    const uint32_t tag = (epoch << 12) | (uint32_t)(h >> 52);
-    const uint64_t mine = ((uint64_t)tag << 32) | (uint32_t)s;
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int SS>
+__device__ __forceinline__ void load_row(const int32_t* sig, int s, int (&row)[SS])
+{
+    const int4* p = reinterpret_cast<const int4*>(sig + (int64_t)s * SS);
+#pragma unroll
+    for (int v = 0; v < SS / 4; ++v) {
+        const int4 x = __ldcg(p + v);
+        row[4 * v] = x.x; row[4 * v + 1] = x.y; row[4 * v + 2] = x.z; row[4 * v + 3] = x.w;
+    }
+}
+
+template <int SS>
+__device__ __forceinline__ void store_row(int32_t* sig, int s, const int (&row)[SS])
+{
+    int4* p = reinterpret_cast<int4*>(sig + (int64_t)s * SS);
+#pragma unroll
+    for (int v = 0; v < SS / 4; ++v)
+        __stcg(p + v, make_int4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]));
+}
+
+// Successors of s for a compile-time alphabet size KC (state-major delta, streamed once per
+// round: evict-first loads).  Vector loads need delta 16-byte aligned (checked on the host).
+template <int KC>
+__device__ __forceinline__ void load_succ(const int32_t* __restrict__ delta, int s, int (&r)[KC])
+{
+    const int32_t* p = delta + (int64_t)s * KC;
+    if constexpr (KC % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < KC / 4; ++v) {
+            const int4 x = __ldcs(reinterpret_cast<const int4*>(p) + v);
+            r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w;
+        }
+    } else if constexpr (KC % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < KC / 2; ++v) {
+            const int2 x = __ldcs(reinterpret_cast<const int2*>(p) + v);
+            r[2 * v] = x.x; r[2 * v + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < KC; ++c) r[c] = __ldcs(p + c);
+    }
+}
+
+template <int KC>
+struct RowOf {
+    static constexpr int SS = (KC + 1 + 3) / 4 * 4;
+};
+
+// Publish s's row (the table may point other states at it) before s enters a slot.
+template <int SS>
+__device__ __forceinline__ void publish_row(const Job& J, int s, const int (&row)[SS])
+{
+    store_row<SS>(J.sig, s, row);
+    __threadfence();
+}
+
+// Insert s into the table; returns the slot of s's group.  A slot holds a state of its group:
+// it is claimed by CAS from empty and lowered to the group's smallest state by atomicMin.  A
+// state's row is published only when it becomes a slot holder, so ordinary members write
+// nothing.  Equality is decided on the full rows, never on the hash.
+template <int SS>
+__device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int (&row)[SS],
+                               int* s_claims)
+{
     uint32_t idx = (uint32_t)h & J.mask;
+    bool published = false;
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
-        uint64_t w = ld_relaxed_u64(&J.table[idx]);
-        while ((uint32_t)(w >> (64 - kEpochBits)) != epoch) {
-            const uint64_t old = atomicCAS((unsigned long long*)&J.table[idx],
-                                           (unsigned long long)w, (unsigned long long)mine);
-            if (old == w) {
+        uint32_t w = ld_acquire_u32(&J.table[idx]);
+        if (w == kEmpty) {
+            if (!published) { publish_row<SS>(J, s, row); published = true; }
+            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
+            if (w == kEmpty) {
                 atomicAdd(s_claims, 1);
                 return idx;
             }
-            w = old;
+            __threadfence();   // acquire: w's row was published before w entered the slot
         }
-        if ((uint32_t)(w >> 32) == tag) {
-            const int t = (int)(uint32_t)w;
-            if (t == s || tuples_equal(J, s, t, leader, ncols)) {
-                if ((uint32_t)s < (uint32_t)t)
-                    atomicMin((unsigned long long*)&J.table[idx], (unsigned long long)mine);
-                return idx;
+        int tr[SS];
+        load_row<SS>(J.sig, (int)w, tr);
+        bool eq = true;
+#pragma unroll
+        for (int c = 0; c < SS; ++c) eq &= (tr[c] == row[c]);
+        if (eq) {
+            if ((uint32_t)s < w) {
+                if (!published) { publish_row<SS>(J, s, row); published = true; }
+                atomicMin(&J.table[idx], (uint32_t)s);
             }
+            return idx;
         }
         idx = (idx + 1) & J.mask;
     }
     set_status(J.ctrl, DFAMIN_EPROBE);
-    return 0xffffffffu;
+    return kFail;
+}
+
+// Chunk v (4 entries) of the row (head, block[succ(s,0)], ..., block[succ(s,ncols-1)], 0...).
+__device__ __forceinline__ void row_chunk(const Job& J, int s, int head, int v, int ncols,
+                                          int (&x)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * v + j;
+        x[j] = (i == 0) ? head : (i <= ncols ? __ldcg(&J.block[succ_col(J, s, i - 1)]) : 0);
+    }
+}
+
+__device__ void publish_row_generic(const Job& J, int s, int head, int nch, int ncols)
+{
+    int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
+    for (int v = 0; v < nch; ++v) {
+        int x[4];
+        row_chunk(J, s, head, v, ncols, x);
+        __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
+    }
+    __threadfence();
+}
+
+// Runtime-width version: s's row is regathered chunk by chunk (L1/L2-hot) for comparisons.
+__device__ uint32_t insert_row_generic(const Job& J, int s, int head, uint64_t h, int nch,
+                                       int ncols, int* s_claims)
+{
+    uint32_t idx = (uint32_t)h & J.mask;
+    bool published = false;
+    for (uint32_t probe = 0; probe <= J.mask; ++probe) {
+        uint32_t w = ld_acquire_u32(&J.table[idx]);
+        if (w == kEmpty) {
+            if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
+            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
+            if (w == kEmpty) {
+                atomicAdd(s_claims, 1);
+                return idx;
+            }
+            __threadfence();
+        }
+        const int4* theirs = reinterpret_cast<const int4*>(J.sig + (int64_t)w * J.sig_stride);
+        bool eq = true;
+        for (int v = 0; v < nch && eq; ++v) {
+            int x[4];
+            row_chunk(J, s, head, v, ncols, x);
+            const int4 b = __ldcg(theirs + v);
+            eq = x[0] == b.x && x[1] == b.y && x[2] == b.z && x[3] == b.w;
+        }
+        if (eq) {
+            if ((uint32_t)s < w) {
+                if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
+                atomicMin(&J.table[idx], (uint32_t)s);
+            }
+            return idx;
+        }
+        idx = (idx + 1) & J.mask;
+    }
+    set_status(J.ctrl, DFAMIN_EPROBE);
+    return kFail;
+}
+
+// Appends (s, slot) for the lanes with `moved` set: one shared atomic per warp.
+__device__ __forceinline__ void append_moved(const Job& J, int c0, bool moved, int s,
+                                             uint32_t slot, int* s_cnt)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, moved);
+    if (m == 0u) return;
+    const int first = __ffs(m) - 1;
+    int pos0 = 0;
+    if ((int)lane == first) pos0 = atomicAdd(s_cnt, __popc(m));
+    pos0 = __shfl_sync(0xffffffffu, pos0, first);
+    if (moved) {
+        const int pos = pos0 + __popc(m & ((1u << lane) - 1u));
+        J.lst_s[c0 + pos] = s;
+        J.lst_slot[c0 + pos] = slot;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-CTA caches for rounds with few blocks.  When the partition has few blocks, most states of
+// a CTA fall into a handful of groups, and every probe of the global table would hit the same
+// few slots and rows (one L2 slice each).  The CTA then keeps, in shared memory, the groups it
+// has already entered (hash, row, global slot) and the rows of leaders it has read.  States are
+// visited in increasing order, tile by tile, and a cache entry is filled only by a state that
+// went through the global table; a later state that finds its row in the cache is larger than
+// that state, so it needs neither the table nor an atomicMin.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kCached = 0x80000000u;  // list slot flag: the low bits index the group cache
+constexpr int kCacheMaxBlocks = 4096;    // rounds that start with at most this many blocks
+constexpr int kLeaderCache = 256;        // leader rows, direct-mapped by leader id
+
+template <int SS>
+struct CtaCache {
+    static constexpr int kSlots = SS <= 8 ? DFAMIN_SLOT_CACHE : DFAMIN_SLOT_CACHE / 2;
+    unsigned long long key[kSlots];
+    uint32_t gslot[kSlots];              // kEmpty = entry unused
+    int gmin[kSlots];
+    int row[kSlots][SS];
+    int lkey[kLeaderCache];
+    int lrow[kLeaderCache][SS];
+};
+
+template <int KC>
+struct CacheOf {
+    using type = CtaCache<RowOf<KC>::SS>;
+};
+template <>
+struct CacheOf<0> {
+    struct type {
+        int unused;
+    };
+};
+
+template <int SS>
+__device__ void cache_clear(CtaCache<SS>& C)
+{
+    for (int i = threadIdx.x; i < CtaCache<SS>::kSlots; i += blockDim.x) C.gslot[i] = kEmpty;
+    for (int i = threadIdx.x; i < kLeaderCache; i += blockDim.x) C.lkey[i] = -1;
+}
+
+template <int KC>
+__device__ void phase_members_cached(const Job& J, int c0, int c1, int* s_claims, int* s_cnt,
+                                     CtaCache<RowOf<KC>::SS>& C)
+{
+    constexpr int SS = RowOf<KC>::SS;
+    constexpr int kSlots = CtaCache<SS>::kSlots;
+    // software pipeline: block[s] and the successor row of the next state are in flight while
+    // the current state is processed
+    int nL = 0, nr[KC];
+    {
+        const int s = c0 + threadIdx.x;
+        if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
+    }
+    for (int base = c0; base < c1; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        int L = nL;
+        int r[KC];
+#pragma unroll
+        for (int c = 0; c < KC; ++c) r[c] = nr[c];
+        if (DFAMIN_PREFETCH) {
+            if (s + (int)blockDim.x < c1) {
+                nL = __ldcg(&J.block[s + blockDim.x]);
+                load_succ<KC>(J.delta, s + blockDim.x, nr);
+            }
+        } else if (s < c1) {
+            L = __ldcg(&J.block[s]);
+            load_succ<KC>(J.delta, s, r);
+        }
+        bool moved = false, fill = false, lfill = false;
+        uint32_t slot = 0;
+        uint64_t h = 0;
+        int row[SS], lr[SS];
+        if (s < c1 && L != s) {
+            const int li = L & (kLeaderCache - 1);
+            if (C.lkey[li] == L) {
+#pragma unroll
+                for (int c = 0; c < SS; ++c) lr[c] = C.lrow[li][c];
+            } else {
+                load_row<SS>(J.sig, L, lr);
+                lfill = true;
+            }
+            row[0] = L;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+#pragma unroll
+            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+            bool same = true;
+#pragma unroll
+            for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
+            if (!same) {
+                h = hash_begin(L);
+#pragma unroll
+                for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
+                h = hash_final(h, L, J.flags);
+                const int ci = (int)(h & (uint64_t)(kSlots - 1));
+                bool hit = false;
+                if (C.gslot[ci] != kEmpty && C.key[ci] == h) {
+                    hit = true;
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) hit &= (C.row[ci][c] == row[c]);
+                }
+                if (hit) {
+                    slot = kCached | (uint32_t)ci;
+                    moved = true;
+                } else {
+                    slot = insert_row<SS>(J, s, h, row, s_claims);
+                    moved = fill = slot != kFail;
+                }
+            }
+        }
+        append_moved(J, c0, moved, s, slot, s_cnt);
+        __syncthreads();                              // lookups of this tile are done
+        if (fill) {
+            const int ci = (int)(h & (uint64_t)(kSlots - 1));
+            if (atomicCAS(&C.gslot[ci], kEmpty, slot) == kEmpty) {
+                C.key[ci] = h;
+#pragma unroll
+                for (int c = 0; c < SS; ++c) C.row[ci][c] = row[c];
+            }
+        }
+        if (lfill) {
+            const int li = L & (kLeaderCache - 1);
+            if (atomicCAS(&C.lkey[li], -1, L) == -1) {
+#pragma unroll
+                for (int c = 0; c < SS; ++c) C.lrow[li][c] = lr[c];
+            }
+        }
+        __syncthreads();                              // fills visible to the next tile
+    }
+}
+
+// ---- phase A: every leader publishes its signature row.  Leaders are kept in a per-CTA list:
+// a leader stays a leader (it is the smallest state of its block and stays in its own group),
+// and every round adds the smallest states of its new groups.
+template <int KC>
+__device__ void phase_leaders(const Job& J, int rank, int T, int nlead, int ncols)
+{
+    const int gid = rank * (int)blockDim.x + (int)threadIdx.x, stride = T * (int)blockDim.x;
+    if constexpr (KC > 0) {
+        constexpr int SS = RowOf<KC>::SS;
+        int ns = 0, nr[KC];
+        if (gid < nlead) {
+            ns = __ldcg(&J.lead[gid]);
+            load_succ<KC>(J.delta, ns, nr);
+        }
+        for (int i = gid; i < nlead; i += stride) {
+            const int s = ns;
+            int r[KC];
+#pragma unroll
+            for (int c = 0; c < KC; ++c) r[c] = nr[c];
+            if (i + stride < nlead) {
+                ns = __ldcg(&J.lead[i + stride]);
+                load_succ<KC>(J.delta, ns, nr);
+            }
+            int row[SS];
+            row[0] = s;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+#pragma unroll
+            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+            store_row<SS>(J.sig, s, row);
+        }
+    } else {
+        const int nch = (ncols + 4) / 4;
+        for (int i = gid; i < nlead; i += stride) {
+            const int s = __ldcg(&J.lead[i]);
+            int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
+            for (int v = 0; v < nch; ++v) {
+                int x[4];
+                row_chunk(J, s, s, v, ncols, x);
+                __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
+            }
+        }
+    }
+}
+
+// ---- phase B: members compare with their leader; those that differ are regrouped.
+// The loop is uniform across the CTA so that appends can be aggregated per warp.
+template <int KC>
+__device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt)
+{
+    if constexpr (KC > 0) {
+        constexpr int SS = RowOf<KC>::SS;
+        int nL = 0, nr[KC];
+        {
+            const int s = c0 + threadIdx.x;
+            if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
+        }
+        for (int base = c0; base < c1; base += blockDim.x) {
+            const int s = base + threadIdx.x;
+            int L = nL;
+            int r[KC];
+#pragma unroll
+            for (int c = 0; c < KC; ++c) r[c] = nr[c];
+            if (DFAMIN_PREFETCH) {
+                if (s + (int)blockDim.x < c1) {
+                    nL = __ldcg(&J.block[s + blockDim.x]);
+                    load_succ<KC>(J.delta, s + blockDim.x, nr);
+                }
+            } else if (s < c1) {
+                L = __ldcg(&J.block[s]);
+                load_succ<KC>(J.delta, s, r);
+            }
+            bool moved = false;
+            uint32_t slot = 0;
+            if (s < c1 && L != s) {
+                int lr[SS];
+                load_row<SS>(J.sig, L, lr);
+                int row[SS];
+                row[0] = L;
+#pragma unroll
+                for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+#pragma unroll
+                for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                bool same = true;
+#pragma unroll
+                for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
+                if (!same) {                          // T(s) != T(leader): regroup
+                    uint64_t h = hash_begin(L);
+#pragma unroll
+                    for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
+                    h = hash_final(h, L, J.flags);
+                    slot = insert_row<SS>(J, s, h, row, s_claims);
+                    moved = slot != kFail;
+                }
+            }
+            append_moved(J, c0, moved, s, slot, s_cnt);
+        }
+    } else {
+        const int nch = (ncols + 4) / 4;
+        for (int base = c0; base < c1; base += blockDim.x) {
+            const int s = base + threadIdx.x;
+            bool moved = false;
+            uint32_t slot = 0;
+            if (s < c1) {
+                const int L = __ldcg(&J.block[s]);
+                if (L != s) {
+                    const int4* lrow =
+                        reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
+                    bool same = true;
+                    uint64_t h = hash_begin(L);
+                    for (int v = 0; v < nch; ++v) {
+                        int x[4];
+                        row_chunk(J, s, L, v, ncols, x);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int i = 4 * v + j;
+                            if (i >= 1 && i <= ncols) h = hash_step(h, x[j]);
+                        }
+                        if (same) {
+                            const int4 l = __ldcg(lrow + v);
+                            same = l.x == x[0] && l.y == x[1] && l.z == x[2] && l.w == x[3];
+                        }
+                    }
+                    if (!same) {
+                        h = hash_final(h, L, J.flags);
+                        slot = insert_row_generic(J, s, L, h, nch, ncols, s_claims);
+                        moved = slot != kFail;
+                    }
+                }
+            }
+            append_moved(J, c0, moved, s, slot, s_cnt);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
 // Team kernel body: one DFA refined by T co-resident CTAs; CTA `rank` owns states [c0, c1).
+// Per round: A (reset last round's slots, leaders publish rows) | B (members) | C (moves).
 // ------------------------------------------------------------------------------------------
 __device__ void write_outputs(const Job& J, int nblocks, int passes)
 {
@@ -305,25 +751,64 @@ __device__ void write_outputs(const Job& J, int nblocks, int passes)
     if (J.status_out) *J.status_out = st;
 }
 
+// Stages (new leader, its group's slot) for the flagged lanes in this CTA's segment of the
+// staging lists (one shared atomic per warp).
+__device__ __forceinline__ void append_pair(const Job& J, int c0, int* cnt, bool flag, int s,
+                                            uint32_t slot)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (m == 0u) return;
+    const int first = __ffs(m) - 1;
+    int pos0 = 0;
+    if ((int)lane == first) pos0 = atomicAdd(cnt, __popc(m));
+    pos0 = __shfl_sync(0xffffffffu, pos0, first);
+    if (flag) {
+        const int pos = c0 + pos0 + __popc(m & ((1u << lane) - 1u));
+        J.stg[pos] = s;
+        J.lst_rst[pos] = slot;
+    }
+}
+
+template <int KC>
 __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
 {
     __shared__ int s_claims;
     __shared__ int s_cnt;
+    __shared__ int s_rst;
+    __shared__ int s_base;
     const int n = J.n, k = J.k;
-    const int chunk = (n + T - 1) / T;
+    // chunks are multiples of 32 states so that every CTA's rows start 16-byte aligned
+    const int chunk = ((n + T - 1) / T + 31) / 32 * 32;
     const int c0 = min(n, rank * chunk), c1 = min(n, c0 + chunk);
     const bool closure = J.levels > 1;
     const bool elide = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY);
     int passes = 0;
+    const bool tw = rank == 0 && threadIdx.x == 0;     // trace writer
+    if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
+    trace_mark(J, tw, 0, 0);
 
-    // ---- phase V: validate delta rows, find the two initial leaders, mark identity letters
+    // ---- phase V: validate delta rows, find the two initial leaders, mark identity letters,
+    //      empty this CTA's slice of the hash table
     {
         bool bad = false;
         const int64_t r0 = (int64_t)c0 * k, r1 = (int64_t)c1 * k;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const int v = __ldg(&J.delta[i]);
-            if ((unsigned)v >= (unsigned)n) bad = true;
-            if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
+        if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
+            const int64_t v0 = r0 / 4, v1 = r1 / 4;   // r0 is a multiple of 4 (chunk % 32 == 0)
+            const int4* d4 = reinterpret_cast<const int4*>(J.delta);
+            for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
+                const int4 v = __ldcs(d4 + i);
+                bad |= ((unsigned)v.x >= (unsigned)n) | ((unsigned)v.y >= (unsigned)n) |
+                       ((unsigned)v.z >= (unsigned)n) | ((unsigned)v.w >= (unsigned)n);
+            }
+            for (int64_t i = v1 * 4 + threadIdx.x; i < r1; i += blockDim.x)
+                bad |= (unsigned)__ldcs(&J.delta[i]) >= (unsigned)n;
+        } else {
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                const int v = __ldcs(&J.delta[i]);
+                if ((unsigned)v >= (unsigned)n) bad = true;
+                if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
+            }
         }
         if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
         int mf = 0x7fffffff, mn = 0x7fffffff;
@@ -336,13 +821,13 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
             if (mf != 0x7fffffff) atomicMax(&J.ctrl->min_f_rev, n - mf);
             if (mn != 0x7fffffff) atomicMax(&J.ctrl->min_n_rev, n - mn);
         }
-        // clear the hash table slice owned by this CTA
         const uint64_t cap = (uint64_t)J.mask + 1;
         const uint64_t per = (cap + T - 1) / T;
         const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
-        for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = 0;
+        for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmpty;
     }
     if (!team_barrier(ts)) goto done;
+    trace_mark(J, tw, 0, 1);
 
     // ---- phase I: initial partition P0 = {F, Q\F} as leader ids
     {
@@ -350,6 +835,12 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
         const int lf = n - rf, ln = n - rn;
         for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
             J.block[s] = is_accepting(J.accept, s) ? lf : ln;
+        if (rank == 0 && threadIdx.x == 0) {
+            int m = 0;
+            if (rf > 0) J.lead[m++] = lf;
+            if (rn > 0) J.lead[m++] = ln;
+            J.ctrl->nlead = m;
+        }
         if (closure && rank == 0 && threadIdx.x == 0) {
             int m = 0;
             for (int a = 0; a < k; ++a)
@@ -358,6 +849,7 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
         }
     }
     if (!team_barrier(ts)) goto done;
+    trace_mark(J, tw, 0, 2);
 
     {
         int count = (ld_volatile(&J.ctrl->min_f_rev) > 0) + (ld_volatile(&J.ctrl->min_n_rev) > 0);
@@ -383,64 +875,125 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
                 }
             }
             if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, i, 3);
         }
 
         const int ncols = k + ncl * lv;
         const int max_passes = J.max_passes;
         unsigned long long claims_seen = 0;
+        int lead_reset_from = ld_volatile(&J.ctrl->nlead);   // initial leaders own no slot
         while (count < n) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
                 break;
             }
             ++passes;
-            const uint32_t epoch = (uint32_t)((passes - 1) % kEpochPeriod) + 1;
-            if (passes > 1 && epoch == 1) {   // epoch wrapped: clear the table slice again
-                const uint64_t cap = (uint64_t)J.mask + 1;
-                const uint64_t per = (cap + T - 1) / T;
-                const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
-                for (uint64_t x = t0 + threadIdx.x; x < t1; x += blockDim.x) J.table[x] = 0;
-                if (!team_barrier(ts)) goto done;
+            // ---- phase A: empty the slots of last round's groups (listed in phase C by each
+            //      group's smallest state), then leaders publish rows
+            {
+                const int nlead = ld_volatile(&J.ctrl->nlead);
+                const int gid = rank * (int)blockDim.x + (int)threadIdx.x;
+                for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x)
+                    J.table[__ldcg(&J.lead_slot[i])] = kEmpty;
+                lead_reset_from = nlead;
+                phase_leaders<KC>(J, rank, T, nlead, ncols);
             }
-            if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; }
             __syncthreads();
+            if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
+            if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, passes, 4);
 
             // ---- phase B: signatures, comparison with the leader, regrouping of the rest
-            for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-                const int L = __ldcg(&J.block[s]);
-                if (L == s) continue;                 // a leader keeps its id
-                uint64_t h = hash_begin(L);
-                bool same = true;
-                for (int c = 0; c < ncols; ++c) {
-                    const int b = __ldcg(&J.block[succ_col(J, s, c)]);
-                    if (same) same = (b == __ldcg(&J.block[succ_col(J, L, c)]));
-                    h = hash_step(h, b);
+            bool use_cache = false;
+            if constexpr (KC > 0) {
+                extern __shared__ __align__(16) unsigned char dsm[];
+                auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
+                use_cache = count <= kCacheMaxBlocks;
+                if (use_cache) {
+                    cache_clear(cache);
+                    __syncthreads();
+                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache);
+                } else {
+                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
                 }
-                if (same) continue;                   // T(s) == T(leader): id unchanged
-                h = hash_final(h, L, J.flags);
-                const uint32_t slot = table_insert(J, s, L, h, epoch, ncols, &s_claims);
-                if (slot == 0xffffffffu) break;
-                const int pos = atomicAdd(&s_cnt, 1);
-                J.lst_s[c0 + pos] = s;
-                J.lst_slot[c0 + pos] = slot;
+            } else {
+                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
             }
             __syncthreads();
             if (threadIdx.x == 0 && s_claims) atomicAdd(&J.ctrl->claims, (unsigned long long)s_claims);
             if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, passes, 5);
 
             const unsigned long long claims_now = ld_acquire_u64(&J.ctrl->claims);
             const int new_groups = (int)(claims_now - claims_seen);
             claims_seen = claims_now;
             if (new_groups == 0) break;               // partition unchanged: stable
 
-            // ---- phase C: moved states take their group's smallest state as id
-            const int cnt = s_cnt;
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                const int s = J.lst_s[c0 + i];
-                const uint32_t slot = J.lst_slot[c0 + i];
-                J.block[s] = (int)(uint32_t)ld_relaxed_u64(&J.table[slot]);
+            // ---- phase C: moved states take their group's smallest state as id; that state
+            //      becomes a leader and lists the group's slot to be emptied next round
+            {
+                const int cnt = s_cnt;
+                if constexpr (KC > 0) {
+                    extern __shared__ __align__(16) unsigned char dsm[];
+                    auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
+                    if (use_cache) {
+                        for (int ci = threadIdx.x; ci < CtaCache<RowOf<KC>::SS>::kSlots;
+                             ci += blockDim.x)
+                            if (cache.gslot[ci] != kEmpty)
+                                cache.gmin[ci] = (int)ld_relaxed_u32(&J.table[cache.gslot[ci]]);
+                        __syncthreads();
+                    }
+                    for (int b = 0; b < cnt; b += blockDim.x) {
+                        const int i = b + threadIdx.x;
+                        bool lead = false;
+                        uint32_t gs = 0;
+                        int s = 0;
+                        if (i < cnt) {
+                            s = J.lst_s[c0 + i];
+                            const uint32_t slot = J.lst_slot[c0 + i];
+                            int m;
+                            if (use_cache && (slot & kCached)) {
+                                const int ci = (int)(slot & ~kCached);
+                                m = cache.gmin[ci];
+                                gs = cache.gslot[ci];
+                            } else {
+                                m = (int)ld_relaxed_u32(&J.table[slot]);
+                                gs = slot;
+                            }
+                            J.block[s] = m;
+                            lead = (m == s);
+                        }
+                        append_pair(J, c0, &s_rst, lead, s, gs);
+                    }
+                } else {
+                    for (int b = 0; b < cnt; b += blockDim.x) {
+                        const int i = b + threadIdx.x;
+                        bool lead = false;
+                        uint32_t gs = 0;
+                        int s = 0;
+                        if (i < cnt) {
+                            s = J.lst_s[c0 + i];
+                            gs = J.lst_slot[c0 + i];
+                            const int m = (int)ld_relaxed_u32(&J.table[gs]);
+                            J.block[s] = m;
+                            lead = (m == s);
+                        }
+                        append_pair(J, c0, &s_rst, lead, s, gs);
+                    }
+                }
+                // publish this CTA's new leaders to the global list (one atomic per CTA)
+                __syncthreads();
+                const int nnew = s_rst;
+                if (threadIdx.x == 0) s_base = nnew ? atomicAdd(&J.ctrl->nlead, nnew) : 0;
+                __syncthreads();
+                const int lbase = s_base;
+                for (int i = threadIdx.x; i < nnew; i += blockDim.x) {
+                    J.lead[lbase + i] = J.stg[c0 + i];
+                    J.lead_slot[lbase + i] = J.lst_rst[c0 + i];
+                }
             }
             if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, passes, 6);
             count += new_groups;
         }
         if (ld_volatile(&J.ctrl->status) != 0) goto done;
@@ -452,6 +1005,7 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
         heads = cta_sum(heads);
         if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
         if (!team_barrier(ts)) goto done;
+        trace_mark(J, tw, passes, 7);
         int offset = 0;
         for (int r = threadIdx.x; r < rank; r += blockDim.x) offset += __ldcg(&J.cta_cnt[r]);
         offset = cta_sum(offset);
@@ -474,16 +1028,21 @@ __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
             if (L != s) J.out_block[s] = __ldcg(&J.out_block[L]);
         }
         if (rank == T - 1 && threadIdx.x == 0) write_outputs(J, total, passes);
+        if (J.trace) {                                // J.trace is uniform over the team
+            if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, passes, 8);
+        }
         return;
     }
 done:
     if (rank == 0 && threadIdx.x == 0) write_outputs(J, 0, passes);
 }
 
-__global__ void __launch_bounds__(kThreads) team_kernel(Job J)
+template <int KC>
+__global__ void __launch_bounds__(kTeamThreads, (KC >= 6 ? DFAMIN_TEAM_MIN_CTAS - 1 : DFAMIN_TEAM_MIN_CTAS)) team_kernel(Job J)
 {
     TeamSync ts{&J.ctrl->bar, &J.ctrl->status, (unsigned long long)gridDim.x, 0ull, J.timeout_ns};
-    team_minimize(J, blockIdx.x, gridDim.x, ts);
+    team_minimize<KC>(J, blockIdx.x, gridDim.x, ts);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -676,9 +1235,11 @@ inline int floor_log2(int64_t n)
 
 struct Layout {
     size_t ctrl, cta_cnt, nonid, zero_end;  // [ctrl .. zero_end) is zeroed per launch
-    size_t block, lst_s, lst_slot, table, cl, cl_letter, total;
+    size_t block, lst_s, lst_slot, lst_rst, lead, lead_slot, stg, table, sig, cl, cl_letter, trace,
+        total;
     uint32_t cap;
     int levels;
+    int sig_stride;
 };
 
 Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
@@ -694,11 +1255,23 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
     L.block = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
     L.lst_s = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
     L.lst_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
+    L.lst_rst = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
+    L.lead = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
+    L.lead_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
+    L.stg = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
     L.cap = next_pow2_u32((uint64_t)n + (uint64_t)n / 2 + 64);
-    L.table = off; off = align_up(off + sizeof(uint64_t) * (size_t)L.cap, A);
+    L.table = off; off = align_up(off + sizeof(uint32_t) * (size_t)L.cap, A);
     L.levels = (o.closure == DFAMIN_CLOSURE_ON) ? floor_log2(n) + 1 : 1;
+    const int64_t kmax = (int64_t)k * L.levels;      // signature columns (upper bound)
+    L.sig_stride = (int)((kmax + 1 + 3) / 4 * 4);
+    L.sig = off; off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);
     L.cl = off;
     off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)k * (size_t)(L.levels - 1), A);
+    L.trace = 0;
+    if (o.flags & DFAMIN_FLAG_TRACE) {
+        L.trace = off;
+        off += DFAMIN_TRACE_BYTES;
+    }
     L.total = off;
     return L;
 }
@@ -713,12 +1286,12 @@ dfamin_status check_options(const dfamin_options& o)
 
 struct DeviceInfo {
     int sms = 0;
-    int team_blocks_per_sm = 0;
     size_t smem_optin = 0;
 };
 
 std::mutex g_mu;
 std::map<int, DeviceInfo> g_dev;
+std::map<std::pair<int, const void*>, int> g_occ;   // (device, kernel) -> CTAs per SM
 
 // Last CUDA failure seen by this thread (dfamin_last_cuda_error).
 thread_local char g_last_error[256] = "";
@@ -731,10 +1304,11 @@ bool cuda_ok(cudaError_t e, const char* what)
     return false;
 }
 
-dfamin_status device_info(DeviceInfo* out)
+dfamin_status device_info(DeviceInfo* out, int* dev_out)
 {
     int dev = 0;
     if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
+    if (dev_out) *dev_out = dev;
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_dev.find(dev);
     if (it != g_dev.end()) { *out = it->second; return DFAMIN_OK; }
@@ -750,10 +1324,6 @@ dfamin_status device_info(DeviceInfo* out)
     if (!cuda_ok(cudaFuncGetAttributes(&fa, small_kernel), "cudaFuncGetAttributes"))
         return DFAMIN_ECUDA;
     d.smem_optin = (size_t)v > fa.sharedSizeBytes ? (size_t)v - fa.sharedSizeBytes : 0;
-    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.team_blocks_per_sm,
-                                                               team_kernel, kThreads, 0),
-                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
-        return DFAMIN_ECUDA;
     if (!cuda_ok(cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)d.smem_optin),
                  "cudaFuncSetAttribute(small_kernel)"))
@@ -761,6 +1331,57 @@ dfamin_status device_info(DeviceInfo* out)
     g_dev[dev] = d;
     *out = d;
     return DFAMIN_OK;
+}
+
+// CTAs per SM of a team kernel launched with `smem` bytes of dynamic shared memory (the
+// attribute allowing that much is set on first use).
+dfamin_status ctas_per_sm(int dev, const void* kernel, size_t smem, int* out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    const auto key = std::make_pair(dev, kernel);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) { *out = it->second; return DFAMIN_OK; }
+    if (smem > 0 &&
+        !cuda_ok(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem),
+                 "cudaFuncSetAttribute(team_kernel)"))
+        return DFAMIN_ECUDA;
+    int b = 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kTeamThreads, smem),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
+        return DFAMIN_ECUDA;
+    g_occ[key] = b;
+    *out = b;
+    return DFAMIN_OK;
+}
+
+// Alphabet sizes with a compile-time kernel; every other size, and every closure run, uses
+// the runtime-width kernel team_kernel<0>.  *smem receives the kernel's dynamic shared memory.
+template <int KC>
+const void* team_entry(size_t* smem)
+{
+    *smem = sizeof(typename CacheOf<KC>::type);
+    return (const void*)team_kernel<KC>;
+}
+
+const void* team_kernel_for(int k, bool closure, const int32_t* delta, size_t* smem)
+{
+    const bool aligned = ((uintptr_t)delta & 15u) == 0;
+    if (!closure && aligned) {
+        switch (k) {
+        case 1: return team_entry<1>(smem);
+        case 2: return team_entry<2>(smem);
+        case 3: return team_entry<3>(smem);
+        case 4: return team_entry<4>(smem);
+        case 5: return team_entry<5>(smem);
+        case 6: return team_entry<6>(smem);
+        case 7: return team_entry<7>(smem);
+        case 8: return team_entry<8>(smem);
+        default: break;
+        }
+    }
+    *smem = 0;
+    return (const void*)team_kernel<0>;
 }
 
 size_t small_smem_bytes(int32_t n, uint32_t* cap_out)
@@ -775,15 +1396,19 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
                          void* ws, size_t ws_bytes, int32_t* passes, int32_t* status,
                          cudaStream_t stream)
 {
-    if (n < 1 || k < 0 || (int64_t)n * (int64_t)k >= ((int64_t)1 << 40)) return DFAMIN_EINVAL;
+    if (n < 1 || n > (1 << 30) || k < 0 || (int64_t)n * (int64_t)k >= ((int64_t)1 << 40))
+        return DFAMIN_EINVAL;
     if ((k > 0 && !delta) || !accept || !out_block || !nblocks || !ws) return DFAMIN_EINVAL;
-    if (((uintptr_t)ws & 255u) != 0) return DFAMIN_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0 || ((uintptr_t)delta & 3u) != 0 ||
+        ((uintptr_t)accept & 3u) != 0)
+        return DFAMIN_EINVAL;
     dfamin_status st = check_options(o);
     if (st != DFAMIN_OK) return st;
     const Layout L = make_layout(n, k, o);
     if (ws_bytes < L.total) return DFAMIN_ENOMEM;
     DeviceInfo di;
-    st = device_info(&di);
+    int dev = 0;
+    st = device_info(&di, &dev);
     if (st != DFAMIN_OK) return st;
 
     unsigned char* base = (unsigned char*)ws;
@@ -803,13 +1428,25 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.block = (int32_t*)(base + L.block);
     J.lst_s = (int32_t*)(base + L.lst_s);
     J.lst_slot = (uint32_t*)(base + L.lst_slot);
-    J.table = (uint64_t*)(base + L.table);
+    J.lst_rst = (uint32_t*)(base + L.lst_rst);
+    J.lead = (int32_t*)(base + L.lead);
+    J.lead_slot = (uint32_t*)(base + L.lead_slot);
+    J.stg = (int32_t*)(base + L.stg);
+    J.table = (uint32_t*)(base + L.table);
     J.mask = L.cap - 1;
+    J.sig = (int32_t*)(base + L.sig);
+    J.sig_stride = L.sig_stride;
     J.cl = (int32_t*)(base + L.cl);
     J.levels = L.levels;
     J.max_passes = o.max_passes > 0 ? o.max_passes : (n < 0x7fffffff ? n + 1 : n);
     J.flags = o.flags;
     J.timeout_ns = kBarrierTimeoutNs;
+    if (o.flags & DFAMIN_FLAG_TRACE) {
+        J.trace = (long long*)(base + L.trace);
+        J.trace_cap = (DFAMIN_TRACE_BYTES / 8 - 1) / 2;
+        if (!cuda_ok(cudaMemsetAsync(J.trace, 0, sizeof(long long), stream), "cudaMemsetAsync(trace)"))
+            return DFAMIN_ECUDA;
+    }
 
     if (!cuda_ok(cudaMemsetAsync(base + L.ctrl, 0, L.zero_end - L.ctrl, stream),
                  "cudaMemsetAsync(ctrl)"))
@@ -822,16 +1459,22 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
         return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
     }
-    int max_ctas = di.sms * di.team_blocks_per_sm;
+    size_t dsmem = 0;
+    const void* kern = team_kernel_for(k, L.levels > 1, delta, &dsmem);
+    int per_sm = 0;
+    st = ctas_per_sm(dev, kern, dsmem, &per_sm);
+    if (st != DFAMIN_OK) return st;
+    int max_ctas = di.sms * per_sm;
     if (max_ctas > kMaxCtas) max_ctas = kMaxCtas;
+    if (max_ctas < 1) return DFAMIN_ECUDA;
     int ctas = o.ctas > 0 ? o.ctas : max_ctas;
     // at least ~2 states per thread per CTA: small DFAs use fewer CTAs (cheaper barriers)
-    const int64_t want = ((int64_t)n + 2 * kThreads - 1) / (2 * kThreads);
+    const int64_t want = ((int64_t)n + 2 * kTeamThreads - 1) / (2 * kTeamThreads);
     if (o.ctas == 0 && want < ctas) ctas = (int)(want > 0 ? want : 1);
     if (ctas > max_ctas) ctas = max_ctas;
     void* args[] = {&J};
-    if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)team_kernel, dim3(ctas),
-                                             dim3(kThreads), args, 0, stream),
+    if (!cuda_ok(cudaLaunchCooperativeKernel(kern, dim3(ctas), dim3(kTeamThreads), args, dsmem,
+                                             stream),
                  "team_kernel cooperative launch"))
         return DFAMIN_ECUDA;
     return DFAMIN_OK;
@@ -856,7 +1499,7 @@ DFAMIN_API void dfamin_default_options(dfamin_options* opt)
 DFAMIN_API dfamin_status dfamin_workspace_size(int32_t n, int32_t k, const dfamin_options* opt,
                                                size_t* bytes)
 {
-    if (n < 1 || k < 0 || !bytes) return DFAMIN_EINVAL;
+    if (n < 1 || n > (1 << 30) || k < 0 || !bytes) return DFAMIN_EINVAL;
     dfamin_options o;
     dfamin_default_options(&o);
     if (opt) o = *opt;
@@ -884,7 +1527,7 @@ DFAMIN_API dfamin_status dfamin_minimize(int32_t n, int32_t k, const int32_t* de
                                          const uint32_t* accept, int32_t* out_block,
                                          int32_t* nblocks, dfamin_stream_t stream)
 {
-    if (n < 1 || k < 0) return DFAMIN_EINVAL;
+    if (n < 1 || n > (1 << 30) || k < 0) return DFAMIN_EINVAL;
     dfamin_options o;
     dfamin_default_options(&o);
     const size_t need = make_layout(n, k, o).total;

@@ -14,13 +14,18 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdfamin.so")
+# DFAMIN_LIBRARY selects another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("DFAMIN_LIBRARY", os.path.join(_HERE, "libdfamin.so"))
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONVERGE, EPROBE = range(7)
 CLOSURE_OFF, CLOSURE_ON = 0, 1
 FLAG_KEEP_IDENTITY = 1
 FLAG_HASH_BLOCK_ONLY = 2
 FLAG_HASH_CONSTANT = 4
+FLAG_TRACE = 8
+TRACE_BYTES = 262144
+TRACE_PHASES = {0: "start", 1: "validate", 2: "init", 3: "closure", 4: "leaders",
+                5: "members", 6: "moves", 7: "count", 8: "canonical"}
 
 # names declared in include/dfamin.h (checked against the library's exports by the tests)
 ABI_FUNCTIONS = (
@@ -165,6 +170,17 @@ def minimize_ex(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
     if rc:
         raise DfaminError(rc, "dfamin_minimize_ex")
     return Result(out_block, scalars)
+
+
+def read_trace(ws: Workspace, n: int, k: int, opt: Options):
+    """Decode the phase trace of the last call that used ``ws`` with ``opt`` (FLAG_TRACE set):
+    a list of (pass, phase_name, t_ns)."""
+    need = workspace_size(n, k, opt)
+    raw = ws.buf[need - TRACE_BYTES: need].cpu().numpy().view(np.int64)
+    cnt = int(min(raw[0], (TRACE_BYTES // 8 - 1) // 2))
+    recs = raw[1: 1 + 2 * cnt].reshape(cnt, 2)
+    return [(int(t) >> 8, TRACE_PHASES.get(int(t) & 255, str(int(t) & 255)), int(ns))
+            for t, ns in recs]
 
 
 def minimize(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
