@@ -122,6 +122,31 @@ dfamin_status dfamin_minimize_ex(int32_t n, int32_t k, const int32_t *delta,
                                  size_t workspace_bytes, int32_t *passes, int32_t *status,
                                  dfamin_stream_t stream);
 
+/*
+ * dfamin_minimize_static - the same minimization as dfamin_minimize_ex, for callers that cannot
+ * allocate device memory: for example a plugin or an embedded runtime whose host owns the whole
+ * device-memory budget, or a latency-critical path where cudaMalloc's implicit device-wide
+ * synchronisation is not acceptable.  It takes no workspace: it runs in a scratch array of
+ * DFAMIN_STATIC_SCRATCH_BYTES that the library places in device memory as a file-scope static
+ * variable, so every GPU that loads the library holds that array until the process exits.  The
+ * paper has no counterpart; it is an engineering addition to the boundary.
+ *   Limit     problems whose dfamin_workspace_size(n, k, opt) exceeds
+ *             DFAMIN_STATIC_SCRATCH_BYTES are rejected with DFAMIN_ENOMEM before anything is
+ *             enqueued (for k = 4 that is n of about one million states).
+ *   Set-up    the first call on a device looks up the array's device address (with that device
+ *             current) and caches it; make that first call before any stream capture.
+ *   Sharing   all calls on a device share the one array and it keeps the last call's contents
+ *             (the call clears what must start at zero).  Calls whose work overlaps on the GPU
+ *             (other streams, other host threads) race on it: serialise them.
+ *   Allocation  none: no cudaMalloc, cudaFree or other allocating routine is called.
+ * The other arguments are those of dfamin_minimize_ex.
+ */
+#define DFAMIN_STATIC_SCRATCH_BYTES (64u << 20)
+dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int32_t *delta,
+                                     const uint32_t *accept, int32_t *out_block,
+                                     int32_t *nblocks, const dfamin_options *opt,
+                                     int32_t *passes, int32_t *status, dfamin_stream_t stream);
+
 /* Text of the last CUDA runtime failure seen by the library on the calling thread ("" if
  * none); meant for diagnostics after DFAMIN_ECUDA / DFAMIN_ENOMEM.  Thread-local storage. */
 const char *dfamin_last_cuda_error(void);

@@ -1480,6 +1480,27 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     return DFAMIN_OK;
 }
 
+// Scratch of dfamin_minimize_static: a file-scope device array (no allocation call).  Host code
+// must not use its name as a device address; the address comes from cudaGetSymbolAddress,
+// looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_static_scratch[DFAMIN_STATIC_SCRATCH_BYTES];
+std::map<int, void*> g_static_addr;
+
+dfamin_status static_scratch_address(void** out)
+{
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_static_addr.find(dev);
+    if (it != g_static_addr.end()) { *out = it->second; return DFAMIN_OK; }
+    void* ptr = nullptr;
+    if (!cuda_ok(cudaGetSymbolAddress(&ptr, g_static_scratch), "cudaGetSymbolAddress(scratch)"))
+        return DFAMIN_ECUDA;
+    g_static_addr[dev] = ptr;
+    *out = ptr;
+    return DFAMIN_OK;
+}
+
 // Library-owned workspaces for dfamin_minimize: one per (device, stream).
 struct OwnedWs {
     void* ptr = nullptr;
@@ -1552,6 +1573,27 @@ DFAMIN_API dfamin_status dfamin_minimize(int32_t n, int32_t k, const int32_t* de
     }
     return launch_one(n, k, delta, accept, out_block, nblocks, o, ws, need, nullptr, nullptr,
                       (cudaStream_t)stream);
+}
+
+DFAMIN_API dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int32_t* delta,
+                                                const uint32_t* accept, int32_t* out_block,
+                                                int32_t* nblocks, const dfamin_options* opt,
+                                                int32_t* passes, int32_t* status,
+                                                dfamin_stream_t stream)
+{
+    dfamin_options o;
+    dfamin_default_options(&o);
+    if (opt) o = *opt;
+    if (n < 1 || n > (1 << 30) || k < 0) return DFAMIN_EINVAL;
+    const dfamin_status st = check_options(o);
+    if (st != DFAMIN_OK) return st;
+    const size_t need = make_layout(n, k, o).total;
+    if (need > (size_t)DFAMIN_STATIC_SCRATCH_BYTES) return DFAMIN_ENOMEM;
+    void* scratch = nullptr;
+    const dfamin_status sa = static_scratch_address(&scratch);
+    if (sa != DFAMIN_OK) return sa;
+    return launch_one(n, k, delta, accept, out_block, nblocks, o, scratch,
+                      (size_t)DFAMIN_STATIC_SCRATCH_BYTES, passes, status, (cudaStream_t)stream);
 }
 
 DFAMIN_API const char* dfamin_last_cuda_error(void) { return g_last_error; }

@@ -35,6 +35,7 @@ ABI_FUNCTIONS = (
     "dfamin_minimize_ex",
     "dfamin_status_string",
     "dfamin_last_cuda_error",
+    "dfamin_minimize_static",
 )
 
 
@@ -68,6 +69,8 @@ def _load():
                                        p, p, p]
     lib.dfamin_status_string.argtypes = [ctypes.c_int]
     lib.dfamin_status_string.restype = ctypes.c_char_p
+    lib.dfamin_minimize_static.argtypes = [i32, i32, p, p, p, p, ctypes.POINTER(Options), p, p, p]
+    lib.dfamin_minimize_static.restype = ctypes.c_int
     lib.dfamin_last_cuda_error.argtypes = []
     lib.dfamin_last_cuda_error.restype = ctypes.c_char_p
     for f in (lib.dfamin_minimize, lib.dfamin_workspace_size, lib.dfamin_minimize_ex):
