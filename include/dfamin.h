@@ -81,7 +81,8 @@ typedef struct {
     uint32_t flags;      /* DFAMIN_FLAG_* */
     int32_t ctas;        /* 0 = automatic; otherwise number of CTAs for one DFA (tuning) */
     int32_t smem_states; /* 0 = automatic; largest n solved by one CTA in shared memory */
-    int32_t reserved[3]; /* must be 0 */
+    int32_t team_states; /* batches: 0 = automatic; states per CTA when sizing a DFA's team */
+    int32_t reserved[2]; /* must be 0 */
 } dfamin_options;
 
 /* Fills *opt with the defaults (closure off, automatic tuning). */
@@ -121,6 +122,46 @@ dfamin_status dfamin_minimize_ex(int32_t n, int32_t k, const int32_t *delta,
                                  const dfamin_options *opt, void *workspace,
                                  size_t workspace_bytes, int32_t *passes, int32_t *status,
                                  dfamin_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Batches: many DFAs minimized in one persistent launch (each exactly as dfamin_minimize_ex
+ * would: Alg. sortPR rounds, Sec. 3.3, optionally on the closed DFA of Alg. transPR, Sec. 3.4).
+ *
+ * A plan holds the host-side schedule for one shape of batch (the per-DFA sizes) and a small
+ * device table (allocated at creation); launches with the same plan can be repeated and
+ * captured in a CUDA graph.  Data of a batch of `count` DFAs, DFA i having n_i states and k_i
+ * letters:
+ *   state_off  HOST int64 [count+1], state_off[0] = 0, state_off[i+1] - state_off[i] = n_i >= 1
+ *   k          HOST int32 [count], k_i >= 0
+ *   delta      device int32, the DFAs' state-major tables concatenated in order (DFA i starts at
+ *              sum_{j<i} n_j k_j); successor ids are LOCAL to their DFA (in [0, n_i))
+ *   accept     device uint32 bitmap over the concatenated states: state s of DFA i is bit
+ *              state_off[i] + s (LSB first)
+ *   out_block  device int32 [state_off[count]]: canonical ids, local to each DFA
+ *   nblocks, passes, status  device int32 [count] (passes and status may be NULL); a DFA with a
+ *              device-detected error gets status != 0 and nblocks = -status, others are unaffected
+ * The options of the plan apply to every DFA (closure, max_passes, flags).  For batches,
+ * opt->smem_states is the largest n solved by one CTA in shared memory, opt->team_states the
+ * states per CTA when sizing a larger DFA's team, opt->ctas a cap on the grid.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct dfamin_batch_plan_s *dfamin_batch_plan;
+
+dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t *state_off, const int32_t *k,
+                                       const dfamin_options *opt, dfamin_batch_plan *plan);
+dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan);
+
+/* Bytes of device workspace a launch with this plan needs (caller-owned, 256-byte aligned). */
+dfamin_status dfamin_batch_workspace_size(dfamin_batch_plan plan, size_t *bytes);
+
+/* Schedule facts: CTAs of the launch, team tickets, total states and transitions. */
+dfamin_status dfamin_batch_plan_info(dfamin_batch_plan plan, int32_t *grid, int64_t *tickets,
+                                     int64_t *states, int64_t *transitions);
+
+/* Enqueue the minimization of every DFA of the plan's batch on `stream`; asynchronous. */
+dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int32_t *delta,
+                                    const uint32_t *accept, int32_t *out_block, int32_t *nblocks,
+                                    int32_t *passes, int32_t *status, void *workspace,
+                                    size_t workspace_bytes, dfamin_stream_t stream);
 
 /*
  * dfamin_minimize_static - the same minimization as dfamin_minimize_ex, for callers that cannot

@@ -1,34 +1,5 @@
-// dfamin: signature-based partition refinement of DFA states on GB300 (sm_103a).
-//
-// The method (arXiv 2410.22764):
-//   * Sec. 2: the result is the coarsest partition of all states that refines {F, Q\F} and is
-//     stable under delta (language equivalence).
-//   * Alg. sortPR (Sec. 3.3): every round gives each state the signature
-//         T(s) = (block[s], block[delta(s,0)], ..., block[delta(s,k-1)])
-//     and regroups the states by equal signature; rounds repeat until the block count stops
-//     changing.  A block may split into many blocks in one round.
-//   * Alg. transPR (Sec. 3.4): optionally the alphabet is first extended with the letters
-//     a^(2^i), i = 1..floor(log2 n), by pointer doubling; A' has the same state equivalence.
-//
-// GB300 design (not the paper's Thrust sort):
-//   * block ids are LEADER ids: the id of a block is its smallest state.  The block of s in
-//     round r+1 is therefore the smallest state with the same signature, which needs no scan;
-//     ids are turned into canonical ranks once, at the end (one scan).
-//   * a state whose signature equals its leader's keeps its id (this is the test of
-//     Alg. naivePR, Sec. 3.2); only the other states are regrouped, through an open-addressing
-//     hash table keyed by a 64-bit hash of T(s).  A table hit is accepted only after the FULL
-//     signature of the slot's state is compared with T(s), so a hash collision can never merge
-//     two groups.  The group id is min(state) by 64-bit atomicMin on the slot.
-//   * the count of blocks after a round is (count before) + (table slots claimed), so
-//     convergence ("count unchanged") is known on the device after one barrier; there is no
-//     host round trip per round.
-//   * one launch runs the whole minimization: a persistent cooperative kernel whose CTAs meet at
-//     bounded barriers (every wait has a deadline and leaves a status code), or, for DFAs that
-//     fit in shared memory, a single CTA with __syncthreads.
-//
-// Readings of the paper (shared with the CPU oracle): block ids are canonical on output; the
-// initial partition is {F, Q\F} without empty parts; a round that leaves the count unchanged
-// ends the loop, and so does reaching count == n.
+// dfamin: single-DFA entry points (dfamin_minimize, _ex, _static) on GB300 (sm_103a).
+// The refinement itself is in refine.cuh; the shared host helpers in host_common.h.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,1003 +11,10 @@
 #include <utility>
 
 #include "dfamin.h"
+#include "refine.cuh"
+#include "host_common.h"
 
-#define DFAMIN_API extern "C" __attribute__((visibility("default")))
-
-namespace {
-
-constexpr int kThreads = 256;             // threads per CTA of the one-CTA kernel
-#ifndef DFAMIN_TEAM_THREADS
-#define DFAMIN_TEAM_THREADS 256           // threads per CTA of the team kernel
-#endif
-#ifndef DFAMIN_TEAM_MIN_CTAS
-#define DFAMIN_TEAM_MIN_CTAS 4            // team kernel: CTAs per SM the register budget targets
-#endif
-#ifndef DFAMIN_PREFETCH
-#define DFAMIN_PREFETCH 1                 // load the next state's block id and row ahead
-#endif
-#ifndef DFAMIN_SLOT_CACHE
-#define DFAMIN_SLOT_CACHE 512             // per-CTA group-cache entries (rows of <= 8 ints)
-#endif
-constexpr int kTeamThreads = DFAMIN_TEAM_THREADS;
-constexpr int kMaxCtas = 8192;            // capacity of the per-CTA count array
-constexpr int64_t kBarrierTimeoutNs = 4000000000ll;        // 4 s per CTA barrier
-constexpr int kSmallMaxStates = 8192;     // largest n for the shared-memory kernel
-
-// ------------------------------------------------------------------------------------------
-// Device state
-// ------------------------------------------------------------------------------------------
-struct Ctrl {                      // zeroed by the host before every launch
-    unsigned long long bar;        // team barrier: arrivals so far (monotonic)
-    unsigned long long claims;     // table slots claimed so far (all rounds)
-    int status;                    // first device-detected error
-    int min_f_rev;                 // n - (smallest accepting state), 0 if none
-    int min_n_rev;                 // n - (smallest rejecting state), 0 if none
-    int ncl_letters;               // letters that get closure columns
-    int nlead;                     // entries in the global leader list
-    int pad[7];
-};
-
-struct Job {
-    int32_t n, k;
-    const int32_t* __restrict__ delta;   // [n*k] state-major, never written
-    const uint32_t* __restrict__ accept; // bitmap
-    int32_t* out_block;                  // [n]
-    int32_t* nblocks_out;                // scalar
-    int32_t* passes_out;                 // scalar or null
-    int32_t* status_out;                 // scalar or null
-    int32_t* block;                      // [n] leader ids
-    int32_t* cl;                         // closure columns [ncl_letters*(levels-1)][n]
-    int32_t* cl_letter;                  // [k] letters with closure columns (compacted)
-    int32_t* nonid;                      // [k] 1 if letter is not the identity
-    uint32_t* table;                     // [mask+1] group slots (smallest state), kEmpty
-    int32_t* sig;                        // [n * sig_stride] signature rows
-    int32_t sig_stride;                  // ints per row, multiple of 4, >= ncols + 1
-    int32_t* lst_s;                      // [n] changed states, per-CTA segments
-    uint32_t* lst_slot;                  // [n] their table slots (or kCached | cache index)
-    uint32_t* lst_rst;                   // [n] slots to empty next round, per-CTA segments
-    int32_t* lead;                       // [n] global leader list (append-only)
-    uint32_t* lead_slot;                 // [n] table slot of each listed leader's group
-    int32_t* stg;                        // [n] per-CTA staging of new leaders
-    int32_t* cta_cnt;                    // [kMaxCtas]
-    Ctrl* ctrl;
-    uint32_t mask;                       // table capacity - 1
-    int32_t levels;                      // closure levels (1 = no closure)
-    int32_t max_passes;
-    uint32_t flags;
-    int64_t timeout_ns;
-    long long* trace;                    // phase trace or null
-    long long trace_cap;                 // records
-};
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-
-__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
-
-__device__ __forceinline__ void set_status(Ctrl* c, int code) { atomicCAS(&c->status, 0, code); }
-
-// One trace record (written by one thread only).
-__device__ __forceinline__ void trace_mark(const Job& J, bool writer, int pass, int phase)
-{
-    if (J.trace && writer) {
-        const long long i = J.trace[0];
-        if (i < J.trace_cap) {
-            J.trace[1 + 2 * i] = ((long long)pass << 8) | phase;
-            J.trace[2 + 2 * i] = (long long)gtimer();
-        }
-        J.trace[0] = i + 1;
-    }
-}
-
-// splitmix64 finalizer (Steele, Lea & Flood 2014); the hash only steers the table probe.
-__device__ __forceinline__ uint64_t fmix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t hash_begin(int leader)
-{
-    return fmix64((uint64_t)(uint32_t)leader * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull);
-}
-__device__ __forceinline__ uint64_t hash_step(uint64_t h, int b)
-{
-    return fmix64(h + 0x9E3779B97F4A7C15ull + (uint64_t)(uint32_t)b);
-}
-__device__ __forceinline__ uint64_t hash_final(uint64_t h, int leader, uint32_t flags)
-{
-    if (flags & DFAMIN_FLAG_HASH_CONSTANT) return 0;
-    if (flags & DFAMIN_FLAG_HASH_BLOCK_ONLY) return hash_begin(leader);
-    return h;
-}
-
-__device__ __forceinline__ int is_accepting(const uint32_t* acc, int s)
-{
-    return (int)((__ldg(&acc[s >> 5]) >> (s & 31)) & 1u);
-}
-
-// Successor of s under signature column c: the k letters, then the closure columns.
-__device__ __forceinline__ int succ_col(const Job& J, int s, int c)
-{
-    if (c < J.k) return __ldg(&J.delta[(int64_t)s * J.k + c]);
-    return __ldcg(&J.cl[(int64_t)(c - J.k) * J.n + s]);
-}
-
-// ------------------------------------------------------------------------------------------
-// Bounded barrier among the T CTAs of a team.  Monotonic arrival counter: barrier number b is
-// passed once the counter reaches b*T.  Every wait has a deadline; on expiry the status word is
-// set and every CTA leaves at its next barrier.  Returns false if the team must stop.
-// ------------------------------------------------------------------------------------------
-struct TeamSync {
-    unsigned long long* bar;
-    int* status;
-    unsigned long long size;
-    unsigned long long seq;   // barriers passed (thread 0's copy is the one used)
-    int64_t timeout_ns;
-};
-
-__device__ __forceinline__ bool team_barrier(TeamSync& ts)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ts.seq += 1;
-        const unsigned long long target = ts.seq * ts.size;
-        __threadfence();
-        atomicAdd(ts.bar, 1ull);
-        int ok = 1;
-        if (ld_acquire_u64(ts.bar) < target) {
-            const uint64_t t0 = gtimer();
-            unsigned sleep_ns = 32;
-            for (;;) {
-                if (ld_acquire_u64(ts.bar) >= target) break;
-                if (ld_volatile(ts.status) != 0) { ok = 0; break; }
-                if ((int64_t)(gtimer() - t0) > ts.timeout_ns) {
-                    atomicCAS(ts.status, 0, (int)DFAMIN_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(sleep_ns);
-                if (sleep_ns < 256) sleep_ns <<= 1;
-            }
-        }
-        __threadfence();
-        if (ld_volatile(ts.status) != 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Exclusive prefix of a 0/1 flag over the CTA's threads; *total receives the CTA sum.
-// Must be called by all threads of the CTA.
-__device__ int cta_scan_flag(int flag, int* total)
-{
-    __shared__ int s_warp[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const unsigned ballot = __ballot_sync(0xffffffffu, flag);
-    const int in_warp = __popc(ballot & ((1u << lane) - 1u));
-    if (lane == 0) s_warp[warp] = __popc(ballot);
-    __syncthreads();
-    if (warp == 0) {
-        int v = lane < nwarps ? s_warp[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
-        }
-        if (lane < nwarps) s_warp[lane] = v;
-    }
-    __syncthreads();
-    const int base = warp ? s_warp[warp - 1] : 0;
-    *total = s_warp[nwarps - 1];
-    __syncthreads();
-    return base + in_warp;
-}
-
-__device__ int cta_sum(int v)
-{
-    __shared__ int s_red[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    int r = 0;
-    for (int w = 0; w < nwarps; ++w) r += s_red[w];
-    __syncthreads();
-    return r;
-}
-
-__device__ int cta_min(int v)
-{
-    __shared__ int s_red[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    int r = s_red[0];
-    for (int w = 1; w < nwarps; ++w) r = min(r, s_red[w]);
-    __syncthreads();
-    return r;
-}
-
-// ------------------------------------------------------------------------------------------
-// Signature rows.  sig[s*SS .. s*SS+SS) holds the full signature of s in the current round,
-// T(s) = (block[s], block[succ(s,0)], ..., block[succ(s,K-1)]), padded with zeros to SS ints
-// (SS a multiple of 4, so rows are read and written as int4).  A leader writes its row in phase
-// A; a member compares its own signature with its leader's row (one sector instead of
-// regathering the leader's successors); a member that differs publishes its row before it
-// enters the hash table, so the table can verify equality against any slot holder's row.
-// ------------------------------------------------------------------------------------------
-constexpr uint32_t kEmpty = 0xffffffffu;
-constexpr uint32_t kFail = 0xffffffffu;
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p)
-{
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-template <int SS>
-__device__ __forceinline__ void load_row(const int32_t* sig, int s, int (&row)[SS])
-{
-    const int4* p = reinterpret_cast<const int4*>(sig + (int64_t)s * SS);
-#pragma unroll
-    for (int v = 0; v < SS / 4; ++v) {
-        const int4 x = __ldcg(p + v);
-        row[4 * v] = x.x; row[4 * v + 1] = x.y; row[4 * v + 2] = x.z; row[4 * v + 3] = x.w;
-    }
-}
-
-template <int SS>
-__device__ __forceinline__ void store_row(int32_t* sig, int s, const int (&row)[SS])
-{
-    int4* p = reinterpret_cast<int4*>(sig + (int64_t)s * SS);
-#pragma unroll
-    for (int v = 0; v < SS / 4; ++v)
-        __stcg(p + v, make_int4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]));
-}
-
-// Successors of s for a compile-time alphabet size KC (state-major delta, streamed once per
-// round: evict-first loads).  Vector loads need delta 16-byte aligned (checked on the host).
-template <int KC>
-__device__ __forceinline__ void load_succ(const int32_t* __restrict__ delta, int s, int (&r)[KC])
-{
-    const int32_t* p = delta + (int64_t)s * KC;
-    if constexpr (KC % 4 == 0) {
-#pragma unroll
-        for (int v = 0; v < KC / 4; ++v) {
-            const int4 x = __ldcs(reinterpret_cast<const int4*>(p) + v);
-            r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w;
-        }
-    } else if constexpr (KC % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < KC / 2; ++v) {
-            const int2 x = __ldcs(reinterpret_cast<const int2*>(p) + v);
-            r[2 * v] = x.x; r[2 * v + 1] = x.y;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < KC; ++c) r[c] = __ldcs(p + c);
-    }
-}
-
-template <int KC>
-struct RowOf {
-    static constexpr int SS = (KC + 1 + 3) / 4 * 4;
-};
-
-// Publish s's row (the table may point other states at it) before s enters a slot.
-template <int SS>
-__device__ __forceinline__ void publish_row(const Job& J, int s, const int (&row)[SS])
-{
-    store_row<SS>(J.sig, s, row);
-    __threadfence();
-}
-
-// Insert s into the table; returns the slot of s's group.  A slot holds a state of its group:
-// it is claimed by CAS from empty and lowered to the group's smallest state by atomicMin.  A
-// state's row is published only when it becomes a slot holder, so ordinary members write
-// nothing.  Equality is decided on the full rows, never on the hash.
-template <int SS>
-__device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int (&row)[SS],
-                               int* s_claims)
-{
-    uint32_t idx = (uint32_t)h & J.mask;
-    bool published = false;
-    for (uint32_t probe = 0; probe <= J.mask; ++probe) {
-        uint32_t w = ld_acquire_u32(&J.table[idx]);
-        if (w == kEmpty) {
-            if (!published) { publish_row<SS>(J, s, row); published = true; }
-            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
-            if (w == kEmpty) {
-                atomicAdd(s_claims, 1);
-                return idx;
-            }
-            __threadfence();   // acquire: w's row was published before w entered the slot
-        }
-        int tr[SS];
-        load_row<SS>(J.sig, (int)w, tr);
-        bool eq = true;
-#pragma unroll
-        for (int c = 0; c < SS; ++c) eq &= (tr[c] == row[c]);
-        if (eq) {
-            if ((uint32_t)s < w) {
-                if (!published) { publish_row<SS>(J, s, row); published = true; }
-                atomicMin(&J.table[idx], (uint32_t)s);
-            }
-            return idx;
-        }
-        idx = (idx + 1) & J.mask;
-    }
-    set_status(J.ctrl, DFAMIN_EPROBE);
-    return kFail;
-}
-
-// Chunk v (4 entries) of the row (head, block[succ(s,0)], ..., block[succ(s,ncols-1)], 0...).
-__device__ __forceinline__ void row_chunk(const Job& J, int s, int head, int v, int ncols,
-                                          int (&x)[4])
-{
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = 4 * v + j;
-        x[j] = (i == 0) ? head : (i <= ncols ? __ldcg(&J.block[succ_col(J, s, i - 1)]) : 0);
-    }
-}
-
-__device__ void publish_row_generic(const Job& J, int s, int head, int nch, int ncols)
-{
-    int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
-    for (int v = 0; v < nch; ++v) {
-        int x[4];
-        row_chunk(J, s, head, v, ncols, x);
-        __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
-    }
-    __threadfence();
-}
-
-// Runtime-width version: s's row is regathered chunk by chunk (L1/L2-hot) for comparisons.
-__device__ uint32_t insert_row_generic(const Job& J, int s, int head, uint64_t h, int nch,
-                                       int ncols, int* s_claims)
-{
-    uint32_t idx = (uint32_t)h & J.mask;
-    bool published = false;
-    for (uint32_t probe = 0; probe <= J.mask; ++probe) {
-        uint32_t w = ld_acquire_u32(&J.table[idx]);
-        if (w == kEmpty) {
-            if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
-            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
-            if (w == kEmpty) {
-                atomicAdd(s_claims, 1);
-                return idx;
-            }
-            __threadfence();
-        }
-        const int4* theirs = reinterpret_cast<const int4*>(J.sig + (int64_t)w * J.sig_stride);
-        bool eq = true;
-        for (int v = 0; v < nch && eq; ++v) {
-            int x[4];
-            row_chunk(J, s, head, v, ncols, x);
-            const int4 b = __ldcg(theirs + v);
-            eq = x[0] == b.x && x[1] == b.y && x[2] == b.z && x[3] == b.w;
-        }
-        if (eq) {
-            if ((uint32_t)s < w) {
-                if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
-                atomicMin(&J.table[idx], (uint32_t)s);
-            }
-            return idx;
-        }
-        idx = (idx + 1) & J.mask;
-    }
-    set_status(J.ctrl, DFAMIN_EPROBE);
-    return kFail;
-}
-
-// Appends (s, slot) for the lanes with `moved` set: one shared atomic per warp.
-__device__ __forceinline__ void append_moved(const Job& J, int c0, bool moved, int s,
-                                             uint32_t slot, int* s_cnt)
-{
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned m = __ballot_sync(0xffffffffu, moved);
-    if (m == 0u) return;
-    const int first = __ffs(m) - 1;
-    int pos0 = 0;
-    if ((int)lane == first) pos0 = atomicAdd(s_cnt, __popc(m));
-    pos0 = __shfl_sync(0xffffffffu, pos0, first);
-    if (moved) {
-        const int pos = pos0 + __popc(m & ((1u << lane) - 1u));
-        J.lst_s[c0 + pos] = s;
-        J.lst_slot[c0 + pos] = slot;
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Per-CTA caches for rounds with few blocks.  When the partition has few blocks, most states of
-// a CTA fall into a handful of groups, and every probe of the global table would hit the same
-// few slots and rows (one L2 slice each).  The CTA then keeps, in shared memory, the groups it
-// has already entered (hash, row, global slot) and the rows of leaders it has read.  States are
-// visited in increasing order, tile by tile, and a cache entry is filled only by a state that
-// went through the global table; a later state that finds its row in the cache is larger than
-// that state, so it needs neither the table nor an atomicMin.
-// ------------------------------------------------------------------------------------------
-constexpr uint32_t kCached = 0x80000000u;  // list slot flag: the low bits index the group cache
-constexpr int kCacheMaxBlocks = 4096;    // rounds that start with at most this many blocks
-constexpr int kLeaderCache = 256;        // leader rows, direct-mapped by leader id
-
-template <int SS>
-struct CtaCache {
-    static constexpr int kSlots = SS <= 8 ? DFAMIN_SLOT_CACHE : DFAMIN_SLOT_CACHE / 2;
-    unsigned long long key[kSlots];
-    uint32_t gslot[kSlots];              // kEmpty = entry unused
-    int gmin[kSlots];
-    int row[kSlots][SS];
-    int lkey[kLeaderCache];
-    int lrow[kLeaderCache][SS];
-};
-
-template <int KC>
-struct CacheOf {
-    using type = CtaCache<RowOf<KC>::SS>;
-};
-template <>
-struct CacheOf<0> {
-    struct type {
-        int unused;
-    };
-};
-
-template <int SS>
-__device__ void cache_clear(CtaCache<SS>& C)
-{
-    for (int i = threadIdx.x; i < CtaCache<SS>::kSlots; i += blockDim.x) C.gslot[i] = kEmpty;
-    for (int i = threadIdx.x; i < kLeaderCache; i += blockDim.x) C.lkey[i] = -1;
-}
-
-template <int KC>
-__device__ void phase_members_cached(const Job& J, int c0, int c1, int* s_claims, int* s_cnt,
-                                     CtaCache<RowOf<KC>::SS>& C)
-{
-    constexpr int SS = RowOf<KC>::SS;
-    constexpr int kSlots = CtaCache<SS>::kSlots;
-    // software pipeline: block[s] and the successor row of the next state are in flight while
-    // the current state is processed
-    int nL = 0, nr[KC];
-    {
-        const int s = c0 + threadIdx.x;
-        if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
-    }
-    for (int base = c0; base < c1; base += blockDim.x) {
-        const int s = base + threadIdx.x;
-        int L = nL;
-        int r[KC];
-#pragma unroll
-        for (int c = 0; c < KC; ++c) r[c] = nr[c];
-        if (DFAMIN_PREFETCH) {
-            if (s + (int)blockDim.x < c1) {
-                nL = __ldcg(&J.block[s + blockDim.x]);
-                load_succ<KC>(J.delta, s + blockDim.x, nr);
-            }
-        } else if (s < c1) {
-            L = __ldcg(&J.block[s]);
-            load_succ<KC>(J.delta, s, r);
-        }
-        bool moved = false, fill = false, lfill = false;
-        uint32_t slot = 0;
-        uint64_t h = 0;
-        int row[SS], lr[SS];
-        if (s < c1 && L != s) {
-            const int li = L & (kLeaderCache - 1);
-            if (C.lkey[li] == L) {
-#pragma unroll
-                for (int c = 0; c < SS; ++c) lr[c] = C.lrow[li][c];
-            } else {
-                load_row<SS>(J.sig, L, lr);
-                lfill = true;
-            }
-            row[0] = L;
-#pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
-#pragma unroll
-            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-            bool same = true;
-#pragma unroll
-            for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
-            if (!same) {
-                h = hash_begin(L);
-#pragma unroll
-                for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
-                h = hash_final(h, L, J.flags);
-                const int ci = (int)(h & (uint64_t)(kSlots - 1));
-                bool hit = false;
-                if (C.gslot[ci] != kEmpty && C.key[ci] == h) {
-                    hit = true;
-#pragma unroll
-                    for (int c = 0; c < SS; ++c) hit &= (C.row[ci][c] == row[c]);
-                }
-                if (hit) {
-                    slot = kCached | (uint32_t)ci;
-                    moved = true;
-                } else {
-                    slot = insert_row<SS>(J, s, h, row, s_claims);
-                    moved = fill = slot != kFail;
-                }
-            }
-        }
-        append_moved(J, c0, moved, s, slot, s_cnt);
-        __syncthreads();                              // lookups of this tile are done
-        if (fill) {
-            const int ci = (int)(h & (uint64_t)(kSlots - 1));
-            if (atomicCAS(&C.gslot[ci], kEmpty, slot) == kEmpty) {
-                C.key[ci] = h;
-#pragma unroll
-                for (int c = 0; c < SS; ++c) C.row[ci][c] = row[c];
-            }
-        }
-        if (lfill) {
-            const int li = L & (kLeaderCache - 1);
-            if (atomicCAS(&C.lkey[li], -1, L) == -1) {
-#pragma unroll
-                for (int c = 0; c < SS; ++c) C.lrow[li][c] = lr[c];
-            }
-        }
-        __syncthreads();                              // fills visible to the next tile
-    }
-}
-
-// ---- phase A: every leader publishes its signature row.  Leaders are kept in a per-CTA list:
-// a leader stays a leader (it is the smallest state of its block and stays in its own group),
-// and every round adds the smallest states of its new groups.
-template <int KC>
-__device__ void phase_leaders(const Job& J, int rank, int T, int nlead, int ncols)
-{
-    const int gid = rank * (int)blockDim.x + (int)threadIdx.x, stride = T * (int)blockDim.x;
-    if constexpr (KC > 0) {
-        constexpr int SS = RowOf<KC>::SS;
-        int ns = 0, nr[KC];
-        if (gid < nlead) {
-            ns = __ldcg(&J.lead[gid]);
-            load_succ<KC>(J.delta, ns, nr);
-        }
-        for (int i = gid; i < nlead; i += stride) {
-            const int s = ns;
-            int r[KC];
-#pragma unroll
-            for (int c = 0; c < KC; ++c) r[c] = nr[c];
-            if (i + stride < nlead) {
-                ns = __ldcg(&J.lead[i + stride]);
-                load_succ<KC>(J.delta, ns, nr);
-            }
-            int row[SS];
-            row[0] = s;
-#pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
-#pragma unroll
-            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-            store_row<SS>(J.sig, s, row);
-        }
-    } else {
-        const int nch = (ncols + 4) / 4;
-        for (int i = gid; i < nlead; i += stride) {
-            const int s = __ldcg(&J.lead[i]);
-            int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
-            for (int v = 0; v < nch; ++v) {
-                int x[4];
-                row_chunk(J, s, s, v, ncols, x);
-                __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
-            }
-        }
-    }
-}
-
-// ---- phase B: members compare with their leader; those that differ are regrouped.
-// The loop is uniform across the CTA so that appends can be aggregated per warp.
-template <int KC>
-__device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt)
-{
-    if constexpr (KC > 0) {
-        constexpr int SS = RowOf<KC>::SS;
-        int nL = 0, nr[KC];
-        {
-            const int s = c0 + threadIdx.x;
-            if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
-        }
-        for (int base = c0; base < c1; base += blockDim.x) {
-            const int s = base + threadIdx.x;
-            int L = nL;
-            int r[KC];
-#pragma unroll
-            for (int c = 0; c < KC; ++c) r[c] = nr[c];
-            if (DFAMIN_PREFETCH) {
-                if (s + (int)blockDim.x < c1) {
-                    nL = __ldcg(&J.block[s + blockDim.x]);
-                    load_succ<KC>(J.delta, s + blockDim.x, nr);
-                }
-            } else if (s < c1) {
-                L = __ldcg(&J.block[s]);
-                load_succ<KC>(J.delta, s, r);
-            }
-            bool moved = false;
-            uint32_t slot = 0;
-            if (s < c1 && L != s) {
-                int lr[SS];
-                load_row<SS>(J.sig, L, lr);
-                int row[SS];
-                row[0] = L;
-#pragma unroll
-                for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
-#pragma unroll
-                for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-                bool same = true;
-#pragma unroll
-                for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
-                if (!same) {                          // T(s) != T(leader): regroup
-                    uint64_t h = hash_begin(L);
-#pragma unroll
-                    for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
-                    h = hash_final(h, L, J.flags);
-                    slot = insert_row<SS>(J, s, h, row, s_claims);
-                    moved = slot != kFail;
-                }
-            }
-            append_moved(J, c0, moved, s, slot, s_cnt);
-        }
-    } else {
-        const int nch = (ncols + 4) / 4;
-        for (int base = c0; base < c1; base += blockDim.x) {
-            const int s = base + threadIdx.x;
-            bool moved = false;
-            uint32_t slot = 0;
-            if (s < c1) {
-                const int L = __ldcg(&J.block[s]);
-                if (L != s) {
-                    const int4* lrow =
-                        reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
-                    bool same = true;
-                    uint64_t h = hash_begin(L);
-                    for (int v = 0; v < nch; ++v) {
-                        int x[4];
-                        row_chunk(J, s, L, v, ncols, x);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int i = 4 * v + j;
-                            if (i >= 1 && i <= ncols) h = hash_step(h, x[j]);
-                        }
-                        if (same) {
-                            const int4 l = __ldcg(lrow + v);
-                            same = l.x == x[0] && l.y == x[1] && l.z == x[2] && l.w == x[3];
-                        }
-                    }
-                    if (!same) {
-                        h = hash_final(h, L, J.flags);
-                        slot = insert_row_generic(J, s, L, h, nch, ncols, s_claims);
-                        moved = slot != kFail;
-                    }
-                }
-            }
-            append_moved(J, c0, moved, s, slot, s_cnt);
-        }
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Team kernel body: one DFA refined by T co-resident CTAs; CTA `rank` owns states [c0, c1).
-// Per round: A (reset last round's slots, leaders publish rows) | B (members) | C (moves).
-// ------------------------------------------------------------------------------------------
-__device__ void write_outputs(const Job& J, int nblocks, int passes)
-{
-    const int st = ld_volatile(&J.ctrl->status);
-    *J.nblocks_out = st ? -st : nblocks;
-    if (J.passes_out) *J.passes_out = passes;
-    if (J.status_out) *J.status_out = st;
-}
-
-// Stages (new leader, its group's slot) for the flagged lanes in this CTA's segment of the
-// staging lists (one shared atomic per warp).
-__device__ __forceinline__ void append_pair(const Job& J, int c0, int* cnt, bool flag, int s,
-                                            uint32_t slot)
-{
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned m = __ballot_sync(0xffffffffu, flag);
-    if (m == 0u) return;
-    const int first = __ffs(m) - 1;
-    int pos0 = 0;
-    if ((int)lane == first) pos0 = atomicAdd(cnt, __popc(m));
-    pos0 = __shfl_sync(0xffffffffu, pos0, first);
-    if (flag) {
-        const int pos = c0 + pos0 + __popc(m & ((1u << lane) - 1u));
-        J.stg[pos] = s;
-        J.lst_rst[pos] = slot;
-    }
-}
-
-template <int KC>
-__device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
-{
-    __shared__ int s_claims;
-    __shared__ int s_cnt;
-    __shared__ int s_rst;
-    __shared__ int s_base;
-    const int n = J.n, k = J.k;
-    // chunks are multiples of 32 states so that every CTA's rows start 16-byte aligned
-    const int chunk = ((n + T - 1) / T + 31) / 32 * 32;
-    const int c0 = min(n, rank * chunk), c1 = min(n, c0 + chunk);
-    const bool closure = J.levels > 1;
-    const bool elide = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY);
-    int passes = 0;
-    const bool tw = rank == 0 && threadIdx.x == 0;     // trace writer
-    if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
-    trace_mark(J, tw, 0, 0);
-
-    // ---- phase V: validate delta rows, find the two initial leaders, mark identity letters,
-    //      empty this CTA's slice of the hash table
-    {
-        bool bad = false;
-        const int64_t r0 = (int64_t)c0 * k, r1 = (int64_t)c1 * k;
-        if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
-            const int64_t v0 = r0 / 4, v1 = r1 / 4;   // r0 is a multiple of 4 (chunk % 32 == 0)
-            const int4* d4 = reinterpret_cast<const int4*>(J.delta);
-            for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
-                const int4 v = __ldcs(d4 + i);
-                bad |= ((unsigned)v.x >= (unsigned)n) | ((unsigned)v.y >= (unsigned)n) |
-                       ((unsigned)v.z >= (unsigned)n) | ((unsigned)v.w >= (unsigned)n);
-            }
-            for (int64_t i = v1 * 4 + threadIdx.x; i < r1; i += blockDim.x)
-                bad |= (unsigned)__ldcs(&J.delta[i]) >= (unsigned)n;
-        } else {
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-                const int v = __ldcs(&J.delta[i]);
-                if ((unsigned)v >= (unsigned)n) bad = true;
-                if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
-            }
-        }
-        if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
-        int mf = 0x7fffffff, mn = 0x7fffffff;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-            if (is_accepting(J.accept, s)) mf = min(mf, s); else mn = min(mn, s);
-        }
-        mf = cta_min(mf);
-        mn = cta_min(mn);
-        if (threadIdx.x == 0) {
-            if (mf != 0x7fffffff) atomicMax(&J.ctrl->min_f_rev, n - mf);
-            if (mn != 0x7fffffff) atomicMax(&J.ctrl->min_n_rev, n - mn);
-        }
-        const uint64_t cap = (uint64_t)J.mask + 1;
-        const uint64_t per = (cap + T - 1) / T;
-        const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
-        for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmpty;
-    }
-    if (!team_barrier(ts)) goto done;
-    trace_mark(J, tw, 0, 1);
-
-    // ---- phase I: initial partition P0 = {F, Q\F} as leader ids
-    {
-        const int rf = ld_volatile(&J.ctrl->min_f_rev), rn = ld_volatile(&J.ctrl->min_n_rev);
-        const int lf = n - rf, ln = n - rn;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
-            J.block[s] = is_accepting(J.accept, s) ? lf : ln;
-        if (rank == 0 && threadIdx.x == 0) {
-            int m = 0;
-            if (rf > 0) J.lead[m++] = lf;
-            if (rn > 0) J.lead[m++] = ln;
-            J.ctrl->nlead = m;
-        }
-        if (closure && rank == 0 && threadIdx.x == 0) {
-            int m = 0;
-            for (int a = 0; a < k; ++a)
-                if (!elide || ld_volatile(&J.nonid[a])) J.cl_letter[m++] = a;
-            J.ctrl->ncl_letters = m;
-        }
-    }
-    if (!team_barrier(ts)) goto done;
-    trace_mark(J, tw, 0, 2);
-
-    {
-        int count = (ld_volatile(&J.ctrl->min_f_rev) > 0) + (ld_volatile(&J.ctrl->min_n_rev) > 0);
-        const int ncl = closure ? ld_volatile(&J.ctrl->ncl_letters) : 0;
-        const int lv = J.levels - 1;
-
-        // ---- closure levels (Alg. transPR): level i of letter a is level i-1 applied twice
-        for (int i = 1; i <= lv && closure; ++i) {
-            for (int j = 0; j < ncl; ++j) {
-                const int a = __ldcg(&J.cl_letter[j]);
-                int32_t* cur = J.cl + ((int64_t)j * lv + (i - 1)) * n;
-                for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
-                    int t;
-                    if (i == 1) {
-                        t = __ldg(&J.delta[(int64_t)q * k + a]);
-                        t = __ldg(&J.delta[(int64_t)t * k + a]);
-                    } else {
-                        const int32_t* prev = cur - n;   // level i-1 of the same letter
-                        t = __ldcg(&prev[q]);
-                        t = __ldcg(&prev[t]);
-                    }
-                    cur[q] = t;
-                }
-            }
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, i, 3);
-        }
-
-        const int ncols = k + ncl * lv;
-        const int max_passes = J.max_passes;
-        unsigned long long claims_seen = 0;
-        int lead_reset_from = ld_volatile(&J.ctrl->nlead);   // initial leaders own no slot
-        while (count < n) {
-            if (passes >= max_passes) {
-                set_status(J.ctrl, DFAMIN_ENOCONVERGE);
-                break;
-            }
-            ++passes;
-            // ---- phase A: empty the slots of last round's groups (listed in phase C by each
-            //      group's smallest state), then leaders publish rows
-            {
-                const int nlead = ld_volatile(&J.ctrl->nlead);
-                const int gid = rank * (int)blockDim.x + (int)threadIdx.x;
-                for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x)
-                    J.table[__ldcg(&J.lead_slot[i])] = kEmpty;
-                lead_reset_from = nlead;
-                phase_leaders<KC>(J, rank, T, nlead, ncols);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, passes, 4);
-
-            // ---- phase B: signatures, comparison with the leader, regrouping of the rest
-            bool use_cache = false;
-            if constexpr (KC > 0) {
-                extern __shared__ __align__(16) unsigned char dsm[];
-                auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
-                use_cache = count <= kCacheMaxBlocks;
-                if (use_cache) {
-                    cache_clear(cache);
-                    __syncthreads();
-                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache);
-                } else {
-                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
-                }
-            } else {
-                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && s_claims) atomicAdd(&J.ctrl->claims, (unsigned long long)s_claims);
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, passes, 5);
-
-            const unsigned long long claims_now = ld_acquire_u64(&J.ctrl->claims);
-            const int new_groups = (int)(claims_now - claims_seen);
-            claims_seen = claims_now;
-            if (new_groups == 0) break;               // partition unchanged: stable
-
-            // ---- phase C: moved states take their group's smallest state as id; that state
-            //      becomes a leader and lists the group's slot to be emptied next round
-            {
-                const int cnt = s_cnt;
-                if constexpr (KC > 0) {
-                    extern __shared__ __align__(16) unsigned char dsm[];
-                    auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
-                    if (use_cache) {
-                        for (int ci = threadIdx.x; ci < CtaCache<RowOf<KC>::SS>::kSlots;
-                             ci += blockDim.x)
-                            if (cache.gslot[ci] != kEmpty)
-                                cache.gmin[ci] = (int)ld_relaxed_u32(&J.table[cache.gslot[ci]]);
-                        __syncthreads();
-                    }
-                    for (int b = 0; b < cnt; b += blockDim.x) {
-                        const int i = b + threadIdx.x;
-                        bool lead = false;
-                        uint32_t gs = 0;
-                        int s = 0;
-                        if (i < cnt) {
-                            s = J.lst_s[c0 + i];
-                            const uint32_t slot = J.lst_slot[c0 + i];
-                            int m;
-                            if (use_cache && (slot & kCached)) {
-                                const int ci = (int)(slot & ~kCached);
-                                m = cache.gmin[ci];
-                                gs = cache.gslot[ci];
-                            } else {
-                                m = (int)ld_relaxed_u32(&J.table[slot]);
-                                gs = slot;
-                            }
-                            J.block[s] = m;
-                            lead = (m == s);
-                        }
-                        append_pair(J, c0, &s_rst, lead, s, gs);
-                    }
-                } else {
-                    for (int b = 0; b < cnt; b += blockDim.x) {
-                        const int i = b + threadIdx.x;
-                        bool lead = false;
-                        uint32_t gs = 0;
-                        int s = 0;
-                        if (i < cnt) {
-                            s = J.lst_s[c0 + i];
-                            gs = J.lst_slot[c0 + i];
-                            const int m = (int)ld_relaxed_u32(&J.table[gs]);
-                            J.block[s] = m;
-                            lead = (m == s);
-                        }
-                        append_pair(J, c0, &s_rst, lead, s, gs);
-                    }
-                }
-                // publish this CTA's new leaders to the global list (one atomic per CTA)
-                __syncthreads();
-                const int nnew = s_rst;
-                if (threadIdx.x == 0) s_base = nnew ? atomicAdd(&J.ctrl->nlead, nnew) : 0;
-                __syncthreads();
-                const int lbase = s_base;
-                for (int i = threadIdx.x; i < nnew; i += blockDim.x) {
-                    J.lead[lbase + i] = J.stg[c0 + i];
-                    J.lead_slot[lbase + i] = J.lst_rst[c0 + i];
-                }
-            }
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, passes, 6);
-            count += new_groups;
-        }
-        if (ld_volatile(&J.ctrl->status) != 0) goto done;
-
-        // ---- canonical ids: rank of each leader among leaders, in state order
-        int heads = 0;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
-            heads += (__ldcg(&J.block[s]) == s);
-        heads = cta_sum(heads);
-        if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
-        if (!team_barrier(ts)) goto done;
-        trace_mark(J, tw, passes, 7);
-        int offset = 0;
-        for (int r = threadIdx.x; r < rank; r += blockDim.x) offset += __ldcg(&J.cta_cnt[r]);
-        offset = cta_sum(offset);
-        int total = 0;
-        if (rank == T - 1) {
-            for (int r = threadIdx.x; r < T; r += blockDim.x) total += __ldcg(&J.cta_cnt[r]);
-            total = cta_sum(total);
-        }
-        for (int base = c0; base < c1; base += blockDim.x) {
-            const int s = base + threadIdx.x;
-            const int head = (s < c1) && (__ldcg(&J.block[s]) == s);
-            int tile_total;
-            const int pre = cta_scan_flag(head, &tile_total);
-            if (head) J.out_block[s] = offset + pre;
-            offset += tile_total;
-        }
-        if (!team_barrier(ts)) goto done;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-            const int L = __ldcg(&J.block[s]);
-            if (L != s) J.out_block[s] = __ldcg(&J.out_block[L]);
-        }
-        if (rank == T - 1 && threadIdx.x == 0) write_outputs(J, total, passes);
-        if (J.trace) {                                // J.trace is uniform over the team
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, passes, 8);
-        }
-        return;
-    }
-done:
-    if (rank == 0 && threadIdx.x == 0) write_outputs(J, 0, passes);
-}
+namespace dfamin_dev {
 
 template <int KC>
 __global__ void __launch_bounds__(kTeamThreads, (KC >= 6 ? DFAMIN_TEAM_MIN_CTAS - 1 : DFAMIN_TEAM_MIN_CTAS)) team_kernel(Job J)
@@ -1045,201 +23,108 @@ __global__ void __launch_bounds__(kTeamThreads, (KC >= 6 ? DFAMIN_TEAM_MIN_CTAS 
     team_minimize<KC>(J, blockIdx.x, gridDim.x, ts);
 }
 
-// ------------------------------------------------------------------------------------------
-// Small kernel: one CTA refines a DFA with n <= kSmallMaxStates entirely in shared memory.
-// Shared table slots are 32-bit: [hash:16 | state:16], 0xffffffff = empty (n <= 65535).
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int s_succ(const Job& J, int s, int c)
-{
-    return succ_col(J, s, c);
-}
-
-__device__ bool s_tuples_equal(const Job& J, const int* sblock, int s, int t, int leader, int ncols)
-{
-    if (sblock[t] != leader) return false;
-    for (int c = 0; c < ncols; ++c)
-        if (sblock[s_succ(J, s, c)] != sblock[s_succ(J, t, c)]) return false;
-    return true;
-}
-
-__device__ void small_minimize(const Job& J, uint32_t cap)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = J.n, k = J.k;
-    int* sblock = (int*)smem;                       // [n]
-    int* spend = sblock + n;                        // [n] slot of a moved state, -1 otherwise
-    uint32_t* stab = (uint32_t*)(spend + n);        // [cap]
-    __shared__ int s_claims, s_bad;
-    const bool closure = J.levels > 1;
-    const bool elide = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY);
-    const uint32_t smask = cap - 1;
-    int passes = 0, count = 0;
-
-    if (threadIdx.x == 0) s_bad = 0;
-    __syncthreads();
-    {
-        bool bad = false;
-        const int64_t total = (int64_t)n * k;
-        for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
-            const int v = __ldg(&J.delta[i]);
-            if ((unsigned)v >= (unsigned)n) bad = true;
-            if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
-        }
-        if (bad) s_bad = 1;
-    }
-    int mf = 0x7fffffff, mn = 0x7fffffff;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        if (is_accepting(J.accept, s)) mf = min(mf, s); else mn = min(mn, s);
-        spend[s] = -1;
-    }
-    mf = cta_min(mf);
-    mn = cta_min(mn);
-    if (s_bad) {
-        if (threadIdx.x == 0) { set_status(J.ctrl, DFAMIN_EINVAL); write_outputs(J, 0, 0); }
-        return;
-    }
-    for (int s = threadIdx.x; s < n; s += blockDim.x)
-        sblock[s] = is_accepting(J.accept, s) ? mf : mn;
-    count = (mf != 0x7fffffff) + (mn != 0x7fffffff);
-    int ncl = 0;
-    const int lv = J.levels - 1;
-    if (closure) {
-        __syncthreads();   // nonid[] complete
-        if (threadIdx.x == 0) {
-            int m = 0;
-            for (int a = 0; a < k; ++a)
-                if (!elide || J.nonid[a]) J.cl_letter[m++] = a;
-            J.ctrl->ncl_letters = m;
-        }
-        __syncthreads();
-        ncl = J.ctrl->ncl_letters;
-        for (int i = 1; i <= lv; ++i) {
-            for (int j = 0; j < ncl; ++j) {
-                const int a = J.cl_letter[j];
-                int32_t* cur = J.cl + ((int64_t)j * lv + (i - 1)) * n;
-                for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    int t;
-                    if (i == 1) {
-                        t = __ldg(&J.delta[(int64_t)q * k + a]);
-                        t = __ldg(&J.delta[(int64_t)t * k + a]);
-                    } else {
-                        const int32_t* prev = cur - n;   // level i-1 of the same letter
-                        t = prev[q];
-                        t = prev[t];
-                    }
-                    cur[q] = t;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const int ncols = k + ncl * lv;
-    __syncthreads();
-
-    while (count < n) {
-        if (passes >= J.max_passes) {
-            if (threadIdx.x == 0) set_status(J.ctrl, DFAMIN_ENOCONVERGE);
-            break;
-        }
-        ++passes;
-        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) stab[i] = 0xffffffffu;
-        if (threadIdx.x == 0) s_claims = 0;
-        __syncthreads();
-        for (int s = threadIdx.x; s < n; s += blockDim.x) {
-            const int L = sblock[s];
-            if (L == s) continue;
-            uint64_t h = hash_begin(L);
-            bool same = true;
-            for (int c = 0; c < ncols; ++c) {
-                const int b = sblock[s_succ(J, s, c)];
-                if (same) same = (b == sblock[s_succ(J, L, c)]);
-                h = hash_step(h, b);
-            }
-            if (same) continue;
-            h = hash_final(h, L, J.flags);
-            const uint32_t tag = (uint32_t)(h >> 48);
-            const uint32_t mine = (tag << 16) | (uint32_t)s;
-            uint32_t idx = (uint32_t)h & smask;
-            uint32_t probe = 0;
-            for (; probe <= smask; ++probe) {
-                uint32_t w = stab[idx];
-                if (w == 0xffffffffu) {
-                    w = atomicCAS(&stab[idx], 0xffffffffu, mine);
-                    if (w == 0xffffffffu) { atomicAdd(&s_claims, 1); break; }
-                }
-                if ((w >> 16) == tag) {
-                    const int t = (int)(w & 0xffffu);
-                    if (s_tuples_equal(J, sblock, s, t, L, ncols)) {
-                        if (s < t) atomicMin(&stab[idx], mine);
-                        break;
-                    }
-                }
-                idx = (idx + 1) & smask;
-            }
-            if (probe > smask) { set_status(J.ctrl, DFAMIN_EPROBE); break; }
-            spend[s] = (int)idx;
-        }
-        __syncthreads();
-        const int new_groups = s_claims;
-        if (ld_volatile(&J.ctrl->status) != 0 || new_groups == 0) break;
-        for (int s = threadIdx.x; s < n; s += blockDim.x) {
-            const int slot = spend[s];
-            if (slot >= 0) { sblock[s] = (int)(stab[slot] & 0xffffu); spend[s] = -1; }
-        }
-        __syncthreads();
-        count += new_groups;
-    }
-    __syncthreads();
-    if (ld_volatile(&J.ctrl->status) != 0) {
-        if (threadIdx.x == 0) write_outputs(J, 0, passes);
-        return;
-    }
-    // canonical ids: ranks of leaders (kept in spend[]), then every state takes its leader's
-    int offset = 0;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int s = base + threadIdx.x;
-        const int head = (s < n) && (sblock[s] == s);
-        int tile_total;
-        const int pre = cta_scan_flag(head, &tile_total);
-        if (head) spend[s] = offset + pre;
-        offset += tile_total;
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < n; s += blockDim.x) J.out_block[s] = spend[sblock[s]];
-    if (threadIdx.x == 0) write_outputs(J, offset, passes);
-}
-
 __global__ void __launch_bounds__(kThreads) small_kernel(Job J, uint32_t cap)
 {
     small_minimize(J, cap);
 }
 
+}  // namespace dfamin_dev
+
 // ------------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------------
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+namespace dfamin_host {
 
-inline uint32_t next_pow2_u32(uint64_t x)
+std::mutex g_mu;
+thread_local char g_last_error[256] = "";
+
+bool cuda_ok(cudaError_t e, const char* what)
 {
-    uint64_t p = 1;
-    while (p < x) p <<= 1;
-    return (uint32_t)p;
+    if (e == cudaSuccess) return true;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", what, cudaGetErrorString(e),
+             (int)e);
+    return false;
 }
 
-inline int floor_log2(int64_t n)
+namespace {
+struct Props {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+std::map<int, Props> g_props;
+std::map<std::pair<std::pair<int, const void*>, std::pair<int, size_t>>, int> g_occ;
+std::map<std::pair<int, const void*>, int> g_attr_set;   // (device, kernel) -> dynamic smem cap
+}  // namespace
+
+dfamin_status device_props(int* dev_out, int* sms, size_t* smem_optin)
 {
-    int l = 0;
-    while (((int64_t)1 << (l + 1)) <= n) ++l;
-    return l;
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
+    if (dev_out) *dev_out = dev;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_props.find(dev);
+    if (it == g_props.end()) {
+        Props pr;
+        int v = 0;
+        if (!cuda_ok(cudaDeviceGetAttribute(&pr.sms, cudaDevAttrMultiProcessorCount, dev),
+                     "cudaDeviceGetAttribute(SMs)"))
+            return DFAMIN_ECUDA;
+        if (!cuda_ok(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                     "cudaDeviceGetAttribute(smem)"))
+            return DFAMIN_ECUDA;
+        pr.smem_optin = (size_t)v;
+        it = g_props.emplace(dev, pr).first;
+    }
+    if (sms) *sms = it->second.sms;
+    if (smem_optin) *smem_optin = it->second.smem_optin;
+    return DFAMIN_OK;
 }
 
+dfamin_status kernel_ctas_per_sm(int dev, const void* kernel, int threads, size_t smem, int* out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    // the kernel may use up to all the opt-in shared memory: set that once per device and
+    // kernel (a smaller value set for one launch would refuse a later, larger one)
+    const auto akey = std::make_pair(dev, kernel);
+    if (!g_attr_set.count(akey)) {
+        cudaFuncAttributes fa;
+        if (!cuda_ok(cudaFuncGetAttributes(&fa, kernel), "cudaFuncGetAttributes")) return DFAMIN_ECUDA;
+        int v = 0;
+        if (!cuda_ok(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                     "cudaDeviceGetAttribute(smem)"))
+            return DFAMIN_ECUDA;
+        const int avail = v - (int)fa.sharedSizeBytes;
+        if (!cuda_ok(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          avail > 0 ? avail : 0),
+                     "cudaFuncSetAttribute(max dynamic shared memory)"))
+            return DFAMIN_ECUDA;
+        g_attr_set[akey] = avail;
+    }
+    if ((long long)smem > (long long)g_attr_set[akey]) return DFAMIN_EINVAL;
+    const auto key = std::make_pair(akey, std::make_pair(threads, smem));
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) { *out = it->second; return DFAMIN_OK; }
+    int b = 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
+        return DFAMIN_ECUDA;
+    g_occ[key] = b;
+    *out = b;
+    return DFAMIN_OK;
+}
+
+}  // namespace dfamin_host
+
+using namespace dfamin_host;
+using namespace dfamin_dev;
+
+namespace {
+
+// Workspace of one DFA: [control | per-CTA counts | identity flags | trace | DFA arrays].
 struct Layout {
     size_t ctrl, cta_cnt, nonid, zero_end;  // [ctrl .. zero_end) is zeroed per launch
-    size_t block, lst_s, lst_slot, lst_rst, lead, lead_slot, stg, table, sig, cl, cl_letter, trace,
-        total;
-    uint32_t cap;
-    int levels;
-    int sig_stride;
+    size_t trace, dfa, total;
+    DfaLayout d;
 };
 
 Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
@@ -1251,108 +136,13 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
     L.cta_cnt = off; off = align_up(off + sizeof(int32_t) * kMaxCtas, A);
     L.nonid = off; off = align_up(off + sizeof(int32_t) * (size_t)(k > 0 ? k : 1), A);
     L.zero_end = off;
-    L.cl_letter = off; off = align_up(off + sizeof(int32_t) * (size_t)(k > 0 ? k : 1), A);
-    L.block = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
-    L.lst_s = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
-    L.lst_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
-    L.lst_rst = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
-    L.lead = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
-    L.lead_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
-    L.stg = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
-    L.cap = next_pow2_u32((uint64_t)n + (uint64_t)n / 2 + 64);
-    L.table = off; off = align_up(off + sizeof(uint32_t) * (size_t)L.cap, A);
-    L.levels = (o.closure == DFAMIN_CLOSURE_ON) ? floor_log2(n) + 1 : 1;
-    const int64_t kmax = (int64_t)k * L.levels;      // signature columns (upper bound)
-    L.sig_stride = (int)((kmax + 1 + 3) / 4 * 4);
-    L.sig = off; off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);
-    L.cl = off;
-    off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)k * (size_t)(L.levels - 1), A);
-    L.trace = 0;
-    if (o.flags & DFAMIN_FLAG_TRACE) {
-        L.trace = off;
-        off += DFAMIN_TRACE_BYTES;
-    }
+    L.trace = off;
+    if (o.flags & DFAMIN_FLAG_TRACE) off += DFAMIN_TRACE_BYTES;
+    L.dfa = off;
+    L.d = make_dfa_layout(n, k, o.closure == DFAMIN_CLOSURE_ON, true);
+    off += L.d.total;
     L.total = off;
     return L;
-}
-
-dfamin_status check_options(const dfamin_options& o)
-{
-    if (o.closure != DFAMIN_CLOSURE_OFF && o.closure != DFAMIN_CLOSURE_ON) return DFAMIN_EINVAL;
-    if (o.max_passes < 0 || o.ctas < 0 || o.smem_states < 0) return DFAMIN_EINVAL;
-    if (o.reserved[0] || o.reserved[1] || o.reserved[2]) return DFAMIN_EINVAL;
-    return DFAMIN_OK;
-}
-
-struct DeviceInfo {
-    int sms = 0;
-    size_t smem_optin = 0;
-};
-
-std::mutex g_mu;
-std::map<int, DeviceInfo> g_dev;
-std::map<std::pair<int, const void*>, int> g_occ;   // (device, kernel) -> CTAs per SM
-
-// Last CUDA failure seen by this thread (dfamin_last_cuda_error).
-thread_local char g_last_error[256] = "";
-
-bool cuda_ok(cudaError_t e, const char* what)
-{
-    if (e == cudaSuccess) return true;
-    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", what, cudaGetErrorString(e),
-             (int)e);
-    return false;
-}
-
-dfamin_status device_info(DeviceInfo* out, int* dev_out)
-{
-    int dev = 0;
-    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
-    if (dev_out) *dev_out = dev;
-    std::lock_guard<std::mutex> lock(g_mu);
-    auto it = g_dev.find(dev);
-    if (it != g_dev.end()) { *out = it->second; return DFAMIN_OK; }
-    DeviceInfo d;
-    int v = 0;
-    if (!cuda_ok(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev),
-                 "cudaDeviceGetAttribute(SMs)"))
-        return DFAMIN_ECUDA;
-    if (!cuda_ok(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
-                 "cudaDeviceGetAttribute(smem)"))
-        return DFAMIN_ECUDA;
-    cudaFuncAttributes fa;
-    if (!cuda_ok(cudaFuncGetAttributes(&fa, small_kernel), "cudaFuncGetAttributes"))
-        return DFAMIN_ECUDA;
-    d.smem_optin = (size_t)v > fa.sharedSizeBytes ? (size_t)v - fa.sharedSizeBytes : 0;
-    if (!cuda_ok(cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)d.smem_optin),
-                 "cudaFuncSetAttribute(small_kernel)"))
-        return DFAMIN_ECUDA;
-    g_dev[dev] = d;
-    *out = d;
-    return DFAMIN_OK;
-}
-
-// CTAs per SM of a team kernel launched with `smem` bytes of dynamic shared memory (the
-// attribute allowing that much is set on first use).
-dfamin_status ctas_per_sm(int dev, const void* kernel, size_t smem, int* out)
-{
-    std::lock_guard<std::mutex> lock(g_mu);
-    const auto key = std::make_pair(dev, kernel);
-    auto it = g_occ.find(key);
-    if (it != g_occ.end()) { *out = it->second; return DFAMIN_OK; }
-    if (smem > 0 &&
-        !cuda_ok(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem),
-                 "cudaFuncSetAttribute(team_kernel)"))
-        return DFAMIN_ECUDA;
-    int b = 0;
-    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kTeamThreads, smem),
-                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
-        return DFAMIN_ECUDA;
-    g_occ[key] = b;
-    *out = b;
-    return DFAMIN_OK;
 }
 
 // Alphabet sizes with a compile-time kernel; every other size, and every closure run, uses
@@ -1384,11 +174,23 @@ const void* team_kernel_for(int k, bool closure, const int32_t* delta, size_t* s
     return (const void*)team_kernel<0>;
 }
 
-size_t small_smem_bytes(int32_t n, uint32_t* cap_out)
+// Fills the device pointers of a DFA's arrays inside a workspace region.
+void bind_dfa_arrays(Job& J, unsigned char* region, const DfaLayout& d)
 {
-    const uint32_t cap = next_pow2_u32((uint64_t)n + (uint64_t)n / 2 + 32);
-    if (cap_out) *cap_out = cap;
-    return sizeof(int32_t) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)cap;
+    J.cl_letter = (int32_t*)(region + d.cl_letter);
+    J.block = (int32_t*)(region + d.block);
+    J.lst_s = (int32_t*)(region + d.lst_s);
+    J.lst_slot = (uint32_t*)(region + d.lst_slot);
+    J.lst_rst = (uint32_t*)(region + d.lst_rst);
+    J.lead = (int32_t*)(region + d.lead);
+    J.lead_slot = (uint32_t*)(region + d.lead_slot);
+    J.stg = (int32_t*)(region + d.stg);
+    J.table = (uint32_t*)(region + d.table);
+    J.mask = d.cap - 1;
+    J.sig = (int32_t*)(region + d.sig);
+    J.sig_stride = d.sig_stride;
+    J.cl = (int32_t*)(region + d.cl);
+    J.levels = d.levels;
 }
 
 dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint32_t* accept,
@@ -1406,9 +208,9 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     if (st != DFAMIN_OK) return st;
     const Layout L = make_layout(n, k, o);
     if (ws_bytes < L.total) return DFAMIN_ENOMEM;
-    DeviceInfo di;
-    int dev = 0;
-    st = device_info(&di, &dev);
+    int dev = 0, sms = 0;
+    size_t smem_optin = 0;
+    st = device_props(&dev, &sms, &smem_optin);
     if (st != DFAMIN_OK) return st;
 
     unsigned char* base = (unsigned char*)ws;
@@ -1417,6 +219,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.k = k;
     J.delta = delta;
     J.accept = accept;
+    J.acc_off = 0;
     J.out_block = out_block;
     J.nblocks_out = nblocks;
     J.passes_out = passes;
@@ -1424,20 +227,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.ctrl = (Ctrl*)(base + L.ctrl);
     J.cta_cnt = (int32_t*)(base + L.cta_cnt);
     J.nonid = (int32_t*)(base + L.nonid);
-    J.cl_letter = (int32_t*)(base + L.cl_letter);
-    J.block = (int32_t*)(base + L.block);
-    J.lst_s = (int32_t*)(base + L.lst_s);
-    J.lst_slot = (uint32_t*)(base + L.lst_slot);
-    J.lst_rst = (uint32_t*)(base + L.lst_rst);
-    J.lead = (int32_t*)(base + L.lead);
-    J.lead_slot = (uint32_t*)(base + L.lead_slot);
-    J.stg = (int32_t*)(base + L.stg);
-    J.table = (uint32_t*)(base + L.table);
-    J.mask = L.cap - 1;
-    J.sig = (int32_t*)(base + L.sig);
-    J.sig_stride = L.sig_stride;
-    J.cl = (int32_t*)(base + L.cl);
-    J.levels = L.levels;
+    bind_dfa_arrays(J, base + L.dfa, L.d);
     J.max_passes = o.max_passes > 0 ? o.max_passes : (n < 0x7fffffff ? n + 1 : n);
     J.flags = o.flags;
     J.timeout_ns = kBarrierTimeoutNs;
@@ -1455,16 +245,19 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     const int small_limit = o.smem_states > 0 ? o.smem_states : 4096;
     uint32_t scap = 0;
     const size_t smem = small_smem_bytes(n, &scap);
-    if (n <= small_limit && n <= kSmallMaxStates && smem <= di.smem_optin) {
+    if (n <= small_limit && n <= kSmallMaxStates && smem + 1024 <= smem_optin) {
+        int per_sm = 0;
+        st = kernel_ctas_per_sm(dev, (const void*)small_kernel, kThreads, smem, &per_sm);
+        if (st != DFAMIN_OK) return st;
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
         return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
     }
     size_t dsmem = 0;
-    const void* kern = team_kernel_for(k, L.levels > 1, delta, &dsmem);
+    const void* kern = team_kernel_for(k, L.d.levels > 1, delta, &dsmem);
     int per_sm = 0;
-    st = ctas_per_sm(dev, kern, dsmem, &per_sm);
+    st = kernel_ctas_per_sm(dev, kern, kTeamThreads, dsmem, &per_sm);
     if (st != DFAMIN_OK) return st;
-    int max_ctas = di.sms * per_sm;
+    int max_ctas = sms * per_sm;
     if (max_ctas > kMaxCtas) max_ctas = kMaxCtas;
     if (max_ctas < 1) return DFAMIN_ECUDA;
     int ctas = o.ctas > 0 ? o.ctas : max_ctas;
@@ -1596,7 +389,7 @@ DFAMIN_API dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int3
                       (size_t)DFAMIN_STATIC_SCRATCH_BYTES, passes, status, (cudaStream_t)stream);
 }
 
-DFAMIN_API const char* dfamin_last_cuda_error(void) { return g_last_error; }
+DFAMIN_API const char* dfamin_last_cuda_error(void) { return dfamin_host::g_last_error; }
 
 DFAMIN_API const char* dfamin_status_string(dfamin_status s)
 {

@@ -36,6 +36,11 @@ ABI_FUNCTIONS = (
     "dfamin_status_string",
     "dfamin_last_cuda_error",
     "dfamin_minimize_static",
+    "dfamin_batch_plan_create",
+    "dfamin_batch_plan_destroy",
+    "dfamin_batch_workspace_size",
+    "dfamin_batch_plan_info",
+    "dfamin_minimize_batch",
 )
 
 
@@ -51,7 +56,8 @@ class DfaminError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("ctas", ctypes.c_int32),
-                ("smem_states", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("smem_states", ctypes.c_int32), ("team_states", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 def _load():
@@ -71,6 +77,16 @@ def _load():
     lib.dfamin_status_string.restype = ctypes.c_char_p
     lib.dfamin_minimize_static.argtypes = [i32, i32, p, p, p, p, ctypes.POINTER(Options), p, p, p]
     lib.dfamin_minimize_static.restype = ctypes.c_int
+    lib.dfamin_batch_plan_create.argtypes = [i32, p, p, ctypes.POINTER(Options),
+                                             ctypes.POINTER(ctypes.c_void_p)]
+    lib.dfamin_batch_plan_destroy.argtypes = [p]
+    lib.dfamin_batch_workspace_size.argtypes = [p, ctypes.POINTER(sz)]
+    lib.dfamin_batch_plan_info.argtypes = [p, p, p, p, p]
+    lib.dfamin_minimize_batch.argtypes = [p, p, p, p, p, p, p, p, sz, p]
+    for f in (lib.dfamin_batch_plan_create, lib.dfamin_batch_plan_destroy,
+              lib.dfamin_batch_workspace_size, lib.dfamin_batch_plan_info,
+              lib.dfamin_minimize_batch):
+        f.restype = ctypes.c_int
     lib.dfamin_last_cuda_error.argtypes = []
     lib.dfamin_last_cuda_error.restype = ctypes.c_char_p
     for f in (lib.dfamin_minimize, lib.dfamin_workspace_size, lib.dfamin_minimize_ex):
@@ -91,11 +107,12 @@ def status_string(code: int) -> str:
 
 
 def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: int = 0,
-            smem_states: int = 0) -> Options:
+            smem_states: int = 0, team_states: int = 0) -> Options:
     o = Options()
     _lib.dfamin_default_options(ctypes.byref(o))
     o.closure = CLOSURE_ON if closure else CLOSURE_OFF
     o.max_passes, o.flags, o.ctas, o.smem_states = max_passes, flags, ctas, smem_states
+    o.team_states = team_states
     return o
 
 
@@ -218,3 +235,83 @@ def minimize_host(n: int, k: int, delta: np.ndarray, accept: np.ndarray, *,
     r = minimize_ex(n, k, d, a, opt=options(closure=closure, flags=flags,
                                             max_passes=max_passes))
     return r.host()
+
+
+# ------------------------------------------------------------------------------------------
+# Batches
+# ------------------------------------------------------------------------------------------
+def pack_batch(dfas):
+    """Concatenate host DFAs (objects with n, k, delta, accept) into the batch layout of the C
+    ABI: (delta int32, accept uint32 bitmap over all states, state_off int64, k int32)."""
+    ns = np.array([d.n for d in dfas], dtype=np.int64)
+    ks = np.array([d.k for d in dfas], dtype=np.int32)
+    state_off = np.zeros(len(dfas) + 1, dtype=np.int64)
+    state_off[1:] = np.cumsum(ns)
+    delta = np.concatenate([np.asarray(d.delta, dtype=np.int32).reshape(-1) for d in dfas]
+                           + [np.zeros(0, np.int32)])
+    bits = np.concatenate([np.unpackbits(np.ascontiguousarray(d.accept, dtype=np.uint32)
+                                         .view(np.uint8), bitorder="little")[: d.n]
+                           for d in dfas])
+    packed = np.packbits(bits, bitorder="little")
+    words = (bits.size + 31) // 32
+    buf = np.zeros(words * 4, dtype=np.uint8)
+    buf[: packed.size] = packed
+    return delta, buf.view("<u4").astype(np.uint32), state_off, ks
+
+
+class BatchPlan:
+    """A dfamin batch plan (host schedule + small device table) for one batch shape."""
+
+    def __init__(self, state_off, k, opt: Options | None = None):
+        self.state_off = np.ascontiguousarray(state_off, dtype=np.int64)
+        self.k = np.ascontiguousarray(k, dtype=np.int32)
+        self.count = int(self.k.size)
+        self.opt = opt or options()
+        self._plan = ctypes.c_void_p(0)
+        rc = _lib.dfamin_batch_plan_create(
+            self.count, self.state_off.ctypes.data_as(ctypes.c_void_p),
+            self.k.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opt),
+            ctypes.byref(self._plan))
+        if rc:
+            raise DfaminError(rc, "dfamin_batch_plan_create")
+        nb = ctypes.c_size_t(0)
+        _lib.dfamin_batch_workspace_size(self._plan, ctypes.byref(nb))
+        self.workspace_bytes = nb.value
+        g, t, st, tr = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _lib.dfamin_batch_plan_info(self._plan, ctypes.byref(g), ctypes.byref(t),
+                                    ctypes.byref(st), ctypes.byref(tr))
+        self.grid, self.tickets, self.states, self.transitions = g.value, t.value, st.value, tr.value
+
+    def close(self):
+        if self._plan and self._plan.value:
+            _lib.dfamin_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, delta: torch.Tensor, accept: torch.Tensor, *, workspace: Workspace | None = None,
+            out_block: torch.Tensor | None = None, per_dfa: torch.Tensor | None = None,
+            stream=None):
+        """Enqueue dfamin_minimize_batch.  Returns (out_block [states], per_dfa [3, count]
+        = nblocks, passes, status) as device tensors."""
+        dev = accept.device
+        ws = (workspace or Workspace(dev)).get(self.workspace_bytes)
+        if out_block is None:
+            out_block = torch.empty(self.states, dtype=torch.int32, device=dev)
+        if per_dfa is None:
+            per_dfa = torch.zeros((3, self.count), dtype=torch.int32, device=dev)
+        rc = _lib.dfamin_minimize_batch(
+            self._plan, _ptr(delta) if self.transitions > 0 else ctypes.c_void_p(0),
+            _ptr(accept), _ptr(out_block), _ptr(per_dfa[0]), _ptr(per_dfa[1]),
+            _ptr(per_dfa[2]), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream_handle(stream))
+        if rc:
+            raise DfaminError(rc, "dfamin_minimize_batch")
+        return out_block, per_dfa
+
+    def split(self, out_block: np.ndarray):
+        """Per-DFA views of a concatenated host out_block."""
+        return [out_block[self.state_off[i]: self.state_off[i + 1]] for i in range(self.count)]
