@@ -261,3 +261,72 @@ def batch_cap_for_transitions(count: int, seed: int, target: int, **kw) -> int:
         else:
             lo = mid + 1
     return lo
+
+
+# ------------------------------------------------------------------------------------------
+# Batches of random DFAs, generated by the multithreaded C version of the same streams
+# ------------------------------------------------------------------------------------------
+_NATIVE = None
+
+
+def _native():
+    """Build (gcc, once) and load inputs_native.c."""
+    global _NATIVE
+    if _NATIVE is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "inputs_native.c")
+        out_dir = os.path.join(here, "_build")
+        lib = os.path.join(out_dir, "libinputs.so")
+        os.makedirs(out_dir, exist_ok=True)
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".{os.getpid()}.tmp"
+            subprocess.run(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp,
+                            src], check=True)
+            os.replace(tmp, lib)
+        h = ctypes.CDLL(lib)
+        h.inputs_random_batch.restype = ctypes.c_int
+        h.inputs_random_batch.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 8 + [ctypes.c_int32]
+        _NATIVE = h
+    return _NATIVE
+
+
+def random_batch(ns, ks, ps, seeds, threads: int | None = None):
+    """Concatenated batch of random DFAs, DFA i being random_dfa(ns[i], ks[i], ps[i], seeds[i]).
+
+    Returns (delta int32, accept uint32 bitmap over the concatenated states, state_off int64,
+    ks int32): the layout of the batch C ABI (successor ids local to each DFA)."""
+    import ctypes
+    import os
+    ns = np.asarray(ns, dtype=np.int64)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    count = ns.size
+    state_off = np.zeros(count + 1, dtype=np.int64)
+    state_off[1:] = np.cumsum(ns)
+    delta_off = np.zeros(count + 1, dtype=np.int64)
+    delta_off[1:] = np.cumsum(ns * ks.astype(np.int64))
+    sub_d = np.array([substream(int(s), TAG_DELTA) for s in seeds], dtype=np.uint64)
+    sub_a = np.array([substream(int(s), TAG_ACCEPT) for s in seeds], dtype=np.uint64)
+    thr = np.array([min(max(int(round(float(p) * (1 << 53))), 0), 1 << 53) for p in ps],
+                   dtype=np.uint64)
+    delta = np.empty(int(delta_off[-1]), dtype=np.int32)
+    accept = np.empty((int(state_off[-1]) + 31) // 32, dtype=np.uint32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    rc = _native().inputs_random_batch(count, p(state_off), p(delta_off), p(ks), p(sub_d),
+                                       p(sub_a), p(thr), p(delta), p(accept),
+                                       threads or max(1, os.cpu_count() or 1))
+    if rc != 0:
+        raise RuntimeError(f"inputs_random_batch failed ({rc})")
+    return delta, accept, state_off, ks
+
+
+def batch_member(delta, accept, state_off, ks, i: int) -> Dfa:
+    """DFA i of a concatenated batch, as a standalone Dfa."""
+    n, k = int(state_off[i + 1] - state_off[i]), int(ks[i])
+    doff = int(np.sum((state_off[1:i + 1] - state_off[:i]) * ks[:i].astype(np.int64)))
+    lo, hi = int(state_off[i]), int(state_off[i + 1])
+    w0, w1 = lo // 32, (hi + 31) // 32
+    bits = unpack_bits(accept[w0:w1], (w1 - w0) * 32)[lo - 32 * w0: hi - 32 * w0]
+    return Dfa(n, k, delta[doff: doff + n * k].copy(), pack_bits(bits))

@@ -68,3 +68,14 @@ def test_batch_sizes_ranges():
     assert (ns2 * ks2).sum() >= 200_000_000
     ns3, ks3, _, _ = I.batch_sizes(4096, 1, n_cap=cap - 1)
     assert (ns3 * ks3).sum() < 200_000_000
+
+
+def test_native_batch_generator_matches_numpy():
+    ns, ks, ps, seeds = I.batch_sizes(40, 7, n_lo=1, n_hi=3000, k_lo=0, k_hi=6)
+    delta, acc, state_off, kk = I.random_batch(ns, ks, ps, seeds, threads=3)
+    for i in range(40):
+        want = I.random_dfa(int(ns[i]), int(ks[i]), float(ps[i]), int(seeds[i]))
+        got = I.batch_member(delta, acc, state_off, kk, i)
+        assert got.n == want.n and got.k == want.k
+        assert np.array_equal(got.delta, want.delta)
+        assert np.array_equal(got.accepting(), want.accepting())

@@ -319,3 +319,14 @@ def test_path_depth_fibonacci(n):
     d = I.path_fib_dfa(n)
     _, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
     assert path_passes(I.fibonacci_word(n)) == (ps, nb)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_inflated_pass_count_from_base(seed):
+    """The relation the full-size test uses: an inflated DFA takes the base DFA's passes, plus
+    one confirming round when the base is already discrete."""
+    m, k, c = 500 + 37 * seed, 1 + seed % 4, 2 + seed % 5
+    d, base = I.inflated_dfa(m, k, c, 0.5, seed, permute=seed % 2 == 0)
+    _, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
+    _, bnb, bp = oracle.moore(base.delta, base.accept, base.n, base.k)
+    assert nb == bnb and ps == bp + (1 if bnb == base.n else 0)
