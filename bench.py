@@ -3,6 +3,7 @@
 n = 10,000,000, permuted ids, seed 1) on one GB300 per rank and print one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload config2|random1k|path|batch4b|batch4a|serve]
 
 A step is one full minimization (every refinement round until the partition is stable,
 plus the canonical renumbering) of the DFA already resident in HBM.  ``value`` is edge visits
@@ -189,10 +190,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="config2",
+                    choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve"])
+    ap.add_argument("--requests", type=int, default=600)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "config2":
+        import bench_workloads
+        return bench_workloads.run(args)
 
     import torch
     from paper_2410_22764_gb300 import dfamin

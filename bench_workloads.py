@@ -1,0 +1,233 @@
+"""Measurement of the other workloads (one JSON line each), selected by
+``python bench.py --workload random1k|path|batch4b|batch4a|serve``.
+
+* random1k  random DFA n = 1,000, k = 2 (one CTA in shared memory): ms per minimization.
+* path      deep-refinement path n = 2^20, k = 2: plain rounds (534,348) against the closure.
+* batch4b   4,096 random DFAs (n log-uniform 100..10^6 capped so that sum n*k = 2e8, k in 2..26,
+            p in 0.1..0.9): one batched launch against one launch per DFA.
+* batch4a   the same 4,096 draws uncapped (~6.5e9 transitions): one batched launch.
+* serve     Poisson request stream through the continuous-batching server at
+            0.5 / 0.8 / 0.95 of its saturated throughput: p50 / p99 latency and DFAs/s.
+Timing: CUDA events on the launching stream, warm-up first, L2 flushed between timed steps
+(a 512 MB write) unless the inputs are larger than L2.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2410_22764_gb300 import dfamin, inputs as I  # noqa: E402
+
+
+def _line(workload, value, unit, ms, steps, warmup, extra, higher=True):
+    line = {"metric": bench.METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": higher, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": workload}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def _time_steps(fn, steps, warmup, flush=None, stream=None):
+    stream = stream or torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return ts
+
+
+def single(args, name, d, closure=False, steps=None, warmup=None):
+    dd, aa = dfamin.to_device(d.delta, d.accept)
+    ws = dfamin.Workspace()
+    opt = dfamin.options(closure=closure)
+    out = torch.empty(d.n, dtype=torch.int32, device="cuda")
+    sc = torch.zeros(3, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    fn = lambda: dfamin.minimize_ex(d.n, d.k, dd, aa, opt=opt, workspace=ws,  # noqa: E731
+                                    out_block=out, scalars=sc)
+    ts = _time_steps(fn, steps or args.steps, max(3, warmup or args.warmup), flush)
+    nb, ps, st = sc.cpu().tolist()
+    assert st == 0
+    ms = statistics.median(ts)
+    return {"name": name, "ms": ms, "passes": ps, "nblocks": nb, "steps": len(ts),
+            "edge_visits_per_s": d.n * d.k * ps / (ms / 1e3), "us_per_pass": 1e3 * ms / max(ps, 1)}
+
+
+def run_random1k(args):
+    d = I.random_dfa(1000, 2, 0.5, 1)
+    r = single(args, "random1k", d, steps=max(args.steps, 200))
+    _line("random DFA n=1000 k=2 p=0.5 seed 1 (one CTA, shared memory)", r["edge_visits_per_s"],
+          "edge-visits/s", r["ms"], r["steps"], max(3, args.warmup), {"result": r})
+
+
+def run_path(args):
+    d = I.path_fib_dfa(1 << 20)
+    clo = single(args, "closure", d, closure=True, steps=10)
+    plain = single(args, "plain", d, steps=2, warmup=3)
+    _line("path DFA n=2^20 k=2, Fibonacci acceptance: closure (Alg. transPR) vs plain rounds",
+          1e3 / clo["ms"], "minimizations/s", clo["ms"], 10, 3,
+          {"closure": clo, "plain": plain, "speedup_closure_vs_plain": plain["ms"] / clo["ms"]})
+
+
+def _batch_inputs(kind):
+    ns, ks, ps, seeds = I.batch_sizes(4096, 1)
+    if kind == "4b":
+        cap = I.batch_cap_for_transitions(4096, 1, 200_000_000)
+        ns, ks, ps, seeds = I.batch_sizes(4096, 1, n_cap=cap)
+    return I.random_batch(ns, ks, ps, seeds)
+
+
+def _per_dfa_launches(delta, acc, state_off, ks, steps):
+    """One dfamin_minimize_ex launch per DFA (each DFA's rows and bitmap 16-byte aligned)."""
+    count, ns = ks.size, np.diff(state_off)
+    doff = np.concatenate([[0], np.cumsum(ns * ks.astype(np.int64))])
+    dpad = np.concatenate([[0], np.cumsum((ns * ks + 3) // 4 * 4)])
+    aoff = np.concatenate([[0], np.cumsum((ns + 127) // 128 * 4)])
+    dbuf = np.zeros(int(dpad[-1]), np.int32)
+    abuf = np.zeros(int(aoff[-1]), np.uint32)
+    for i in range(count):
+        m = I.batch_member(delta, acc, state_off, ks, i)
+        dbuf[dpad[i]: dpad[i] + m.delta.size] = m.delta
+        abuf[aoff[i]: aoff[i] + m.accept.size] = m.accept
+    db, ab = torch.from_numpy(dbuf).cuda(), torch.from_numpy(abuf.view(np.int32)).cuda()
+    out = torch.empty(int(state_off[-1]), dtype=torch.int32, device="cuda")
+    sc = torch.zeros((count, 3), dtype=torch.int32, device="cuda")
+    wsb = max(dfamin.workspace_size(int(ns[i]), int(ks[i])) for i in range(count))
+    ws = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+    lib, opt = dfamin.lib(), dfamin.options()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P = ctypes.c_void_p
+
+    def fn():
+        for i in range(count):
+            base = sc.data_ptr() + 12 * i
+            rc = lib.dfamin_minimize_ex(
+                int(ns[i]), int(ks[i]), P(db.data_ptr() + 4 * int(dpad[i])),
+                P(ab.data_ptr() + 4 * int(aoff[i])), P(out.data_ptr() + 4 * int(state_off[i])),
+                P(base), ctypes.byref(opt), P(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                P(base + 4), P(base + 8), st)
+            assert rc == 0
+    ts = _time_steps(fn, steps, 1)
+    return statistics.median(ts), out.cpu().numpy(), sc.cpu().numpy()
+
+
+def run_batch(args, kind):
+    delta, acc, state_off, ks = _batch_inputs(kind)
+    plan = dfamin.BatchPlan(state_off, ks, dfamin.options())
+    dd = torch.from_numpy(delta).cuda()
+    aa = torch.from_numpy(acc.view(np.int32)).cuda()
+    ws = dfamin.Workspace()
+    out = torch.empty(plan.states, dtype=torch.int32, device="cuda")
+    per = torch.zeros((3, plan.count), dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    fn = lambda: plan.run(dd, aa, workspace=ws, out_block=out, per_dfa=per)  # noqa: E731
+    steps = max(3, min(args.steps, 10 if kind == "4b" else 5))
+    ts = _time_steps(fn, steps, max(3, args.warmup), flush)
+    p = per.cpu().numpy()
+    assert (p[2] == 0).all()
+    ms = statistics.median(ts)
+    visits = int((np.diff(state_off) * ks.astype(np.int64) * p[1]).sum())
+    extra = {"batched_ms": ms, "dfas": int(plan.count), "states": int(plan.states),
+             "transitions": int(plan.transitions), "grid": plan.grid, "tickets": plan.tickets,
+             "dfas_per_s": plan.count / (ms / 1e3), "gpu_launches": steps,
+             "workspace_gb": plan.workspace_bytes / 1e9}
+    if kind == "4b":
+        pms, pout, psc = _per_dfa_launches(delta, acc, state_off, ks, 2)
+        assert np.array_equal(pout, out.cpu().numpy()) and np.array_equal(psc[:, 0], p[0])
+        extra.update({"per_dfa_launches_ms": pms, "batched_speedup": pms / ms})
+    desc = ("4,096 random DFAs, n log-uniform 100..1e6, k 2..26, p 0.1..0.9, seed 1" +
+            (", n capped so that sum n*k = 2e8" if kind == "4b" else ", as drawn"))
+    _line(desc, visits / (ms / 1e3), "edge-visits/s", ms, steps, max(3, args.warmup), extra)
+
+
+def _serve_pool(pool, seed=5):
+    """Request pool with the served-stream distribution: 5% path DFAs (n = 65,536), the rest
+    half uniform random, half inflated (c = 4); n log-uniform 1e3..4e6, k in 2..8."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(pool):
+        if rng.random() < 0.05:
+            out.append(I.path_fib_dfa(65536))
+            continue
+        n = int(round(10 ** rng.uniform(3, np.log10(4e6))))
+        k = int(rng.integers(2, 9))
+        if rng.random() < 0.5:
+            out.append(I.random_dfa(n, k, 0.5, int(rng.integers(1 << 30))))
+        else:
+            m = max(1, n // 4)
+            out.append(I.inflated_dfa(m, k, 4, 0.5, int(rng.integers(1 << 30)), permute=False)[0])
+    return out
+
+
+def run_serve(args):
+    from paper_2410_22764_gb300 import serve
+    pool = _serve_pool(64)
+    R = args.requests
+    stream_reqs = [pool[i % len(pool)] for i in range(R)]
+
+    def go(rate):
+        srv = serve.Server(budget_bytes=48 << 30, streams=4)
+        rng = np.random.default_rng(11)
+        gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
+        t0 = time.perf_counter()
+        arrive = t0 + np.cumsum(gaps)
+        i = 0
+        while i < R or not srv.idle():
+            now = time.perf_counter()
+            while i < R and arrive[i] <= now:
+                d = stream_reqs[i]
+                srv.submit(d.n, d.k, d.delta, d.accept, arrival=float(arrive[i]))
+                i += 1
+            if not srv.step():
+                time.sleep(20e-6)
+        t1 = time.perf_counter()
+        lat = np.array([r.latency for r in srv.completed if r.status == 0])
+        bad = sum(1 for r in srv.completed if r.status != 0)
+        return {"rate_req_per_s": rate, "dfas_per_s": R / (t1 - t0),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "failed": bad,
+                "batches": srv.stats.batches, "max_inflight": srv.stats.max_inflight,
+                "max_device_overlap": srv.max_device_overlap(), "escalated": srv.stats.escalated}
+
+    go(0)                                               # warm-up (allocator, plans)
+    sat = go(0)
+    runs = {"saturated": sat}
+    for rho in (0.5, 0.8, 0.95):
+        runs[f"rho_{rho}"] = go(rho * sat["dfas_per_s"])
+    _line(f"served Poisson stream, {R} requests drawn from a pool of 64 DFAs (n log-uniform "
+          "1e3..4e6, k 2..8, 50% random / 50% inflated c=4, 5% path n=65536), HBM budget 48 GB",
+          sat["dfas_per_s"], "DFAs/s", 1e3 / sat["dfas_per_s"], R, 1, {"serve": runs})
+
+
+def run(args):
+    torch.cuda.set_device(0)
+    if args.workload == "random1k":
+        run_random1k(args)
+    elif args.workload == "path":
+        run_path(args)
+    elif args.workload in ("batch4b", "batch4a"):
+        run_batch(args, args.workload[-2:])
+    elif args.workload == "serve":
+        run_serve(args)
+    return 0

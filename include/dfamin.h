@@ -148,6 +148,9 @@ typedef struct dfamin_batch_plan_s *dfamin_batch_plan;
 
 dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t *state_off, const int32_t *k,
                                        const dfamin_options *opt, dfamin_batch_plan *plan);
+/* Destroy only after every launch that used the plan has completed.  Plan creation and
+ * destruction use stream-ordered allocation on a library stream: they never wait for work on
+ * other streams. */
 dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan);
 
 /* Bytes of device workspace a launch with this plan needs (caller-owned, 256-byte aligned). */

@@ -20,6 +20,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -176,6 +178,25 @@ struct dfamin_batch_plan_s {
 namespace {
 
 constexpr int kBatchSmallDefault = 2048;     // n up to this: one CTA in shared memory
+
+// Plans keep their descriptor table in stream-ordered memory (cudaMallocAsync / cudaFreeAsync
+// on a library stream per device), so that creating or destroying a plan never waits for work
+// running on other streams.
+std::map<int, cudaStream_t> g_plan_streams;
+
+dfamin_status plan_stream(int dev, cudaStream_t* out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_plan_streams.find(dev);
+    if (it == g_plan_streams.end()) {
+        cudaStream_t s = nullptr;
+        if (!cuda_ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate"))
+            return DFAMIN_ECUDA;
+        it = g_plan_streams.emplace(dev, s).first;
+    }
+    *out = it->second;
+    return DFAMIN_OK;
+}
 constexpr int kBatchTeamStatesDefault = 16384;
 
 size_t cache_bytes_for(int k, bool closure)
@@ -308,14 +329,22 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
     P->tickets = team_sum;
     P->grid = (int)std::min<int64_t>(grid_max, team_sum);
 
-    if (!cuda_ok(cudaMalloc(&P->d_desc, sizeof(BatchDesc) * (size_t)count), "cudaMalloc(plan)")) {
+    cudaStream_t ps = nullptr;
+    st = plan_stream(dev, &ps);
+    if (st != DFAMIN_OK) {
+        delete P;
+        return st;
+    }
+    if (!cuda_ok(cudaMallocAsync((void**)&P->d_desc, sizeof(BatchDesc) * (size_t)count, ps),
+                 "cudaMallocAsync(plan)")) {
         delete P;
         return DFAMIN_ENOMEM;
     }
-    if (!cuda_ok(cudaMemcpy(P->d_desc, P->desc.data(), sizeof(BatchDesc) * (size_t)count,
-                            cudaMemcpyHostToDevice),
-                 "cudaMemcpy(plan)")) {
-        cudaFree(P->d_desc);
+    if (!cuda_ok(cudaMemcpyAsync(P->d_desc, P->desc.data(), sizeof(BatchDesc) * (size_t)count,
+                                 cudaMemcpyHostToDevice, ps),
+                 "cudaMemcpyAsync(plan)") ||
+        !cuda_ok(cudaStreamSynchronize(ps), "cudaStreamSynchronize(plan)")) {
+        cudaFreeAsync(P->d_desc, ps);
         delete P;
         return DFAMIN_ECUDA;
     }
@@ -326,7 +355,10 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
 DFAMIN_API dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan)
 {
     if (!plan) return DFAMIN_EINVAL;
-    if (plan->d_desc) cudaFree(plan->d_desc);
+    if (plan->d_desc) {
+        cudaStream_t ps = nullptr;
+        if (plan_stream(plan->dev, &ps) == DFAMIN_OK) cudaFreeAsync(plan->d_desc, ps);
+    }
     delete plan;
     return DFAMIN_OK;
 }

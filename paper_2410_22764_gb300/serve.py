@@ -1,0 +1,235 @@
+"""Continuous-batching minimization server over the dfamin batch ABI.
+
+Requests (host DFAs) arrive at any time.  The scheduler admits them in arrival order while the
+device memory they need fits in an HBM budget, packs everything admitted since the last launch
+into one batch (one persistent launch, ``dfamin_minimize_batch``) on a free stream, and keeps
+several batches in flight at once, so work of requests that arrived while others were running
+overlaps on the device.  Finished batches are found by polling their events; their results are
+copied back asynchronously and their memory returns to the budget.
+
+Deep-refinement requests are run first with a pass cap; those that hit it
+(``DFAMIN_ENOCONVERGE``) are rerun on the partial transitive closure (Alg. transPR, Sec. 3.4),
+which has the same state equivalence and needs logarithmically many rounds on path-like DFAs.
+The returned partition is the same either way; ``passes`` is the count of the run that
+finished.
+
+All device work goes through the C ABI; this module only schedules and marshals.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import dfamin
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    k: int
+    delta: np.ndarray
+    accept: np.ndarray
+    arrival: float
+    closure: bool = False
+    nbytes: int = 0
+    admitted: float | None = None
+    done: float | None = None
+    out_block: np.ndarray | None = None
+    nblocks: int | None = None
+    passes: int | None = None
+    status: int | None = None
+    attempts: int = 0
+    cancelled: bool = False
+
+    @property
+    def latency(self) -> float | None:
+        return None if self.done is None else self.done - self.arrival
+
+
+@dataclass
+class _Batch:
+    reqs: list
+    closure: bool
+    stream_idx: int
+    plan: object
+    tensors: list
+    host_out: torch.Tensor
+    host_per: torch.Tensor
+    state_off: np.ndarray
+    ev_start: torch.cuda.Event
+    ev_end: torch.cuda.Event
+    nbytes: int
+
+
+@dataclass
+class ServerStats:
+    batches: int = 0
+    max_inflight: int = 0
+    escalated: int = 0
+    rejected: int = 0
+    intervals: list = field(default_factory=list)   # (start_ms, end_ms) of every batch on device
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 32 << 30, streams: int = 4, max_batch: int = 1024,
+                 pass_cap: int = 64, device: str | torch.device = "cuda", flags: int = 0):
+        self.device = torch.device(device)
+        self.budget = int(budget_bytes)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.free = list(range(streams))
+        self.max_batch = max_batch
+        self.pass_cap = pass_cap
+        self.flags = flags
+        self.pending: deque[Request] = deque()
+        self.inflight: list[_Batch] = []
+        self.used = 0
+        self.completed: list[Request] = []
+        self.stats = ServerStats()
+        self._next_id = 0
+        self._base = torch.cuda.Event(enable_timing=True)
+        self._base.record(torch.cuda.current_stream(self.device))
+
+    # ---------------------------------------------------------------- requests
+    def request_bytes(self, n: int, k: int, closure: bool) -> int:
+        """Device bytes one request holds while in flight: inputs, outputs and its share of the
+        batch workspace (bounded by the single-DFA workspace)."""
+        ws = dfamin.workspace_size(n, k, dfamin.options(closure=closure))
+        return ws + 4 * n * k + 4 * ((n + 31) // 32) + 4 * n + 4096
+
+    def submit(self, n: int, k: int, delta: np.ndarray, accept: np.ndarray,
+               arrival: float | None = None) -> Request:
+        r = Request(self._next_id, n, k, np.ascontiguousarray(delta, dtype=np.int32),
+                    np.ascontiguousarray(accept, dtype=np.uint32),
+                    time.perf_counter() if arrival is None else arrival)
+        self._next_id += 1
+        r.nbytes = self.request_bytes(n, k, True)   # admit for the worst case (closure rerun)
+        if r.nbytes > self.budget:
+            r.status = dfamin.ENOMEM
+            r.done = time.perf_counter()
+            self.stats.rejected += 1
+            self.completed.append(r)
+            return r
+        self.pending.append(r)
+        return r
+
+    def cancel(self, r: Request) -> bool:
+        """Withdraw a request that has not been admitted yet."""
+        if r in self.pending:
+            self.pending.remove(r)
+            r.cancelled = True
+            r.done = time.perf_counter()
+            self.completed.append(r)
+            return True
+        return False
+
+    # ---------------------------------------------------------------- scheduling
+    def idle(self) -> bool:
+        return not self.pending and not self.inflight
+
+    def step(self) -> bool:
+        """One scheduler iteration: retire finished batches, then launch one new batch if a
+        stream is free and something fits.  Returns True if anything happened."""
+        progressed = False
+        for b in list(self.inflight):
+            if b.ev_end.query():
+                self._finish(b)
+                progressed = True
+        if self.free and self.pending:
+            reqs = []
+            head_closure = self.pending[0].closure
+            budget_left = self.budget - self.used
+            while (self.pending and len(reqs) < self.max_batch
+                   and self.pending[0].closure == head_closure
+                   and self.pending[0].nbytes <= budget_left):
+                r = self.pending.popleft()
+                budget_left -= r.nbytes
+                reqs.append(r)
+            if reqs:
+                self._launch(reqs, head_closure)
+                progressed = True
+        return progressed
+
+    def drain(self, poll_s: float = 20e-6):
+        while not self.idle():
+            if not self.step():
+                time.sleep(poll_s)
+
+    def _launch(self, reqs, closure: bool):
+        si = self.free.pop()
+        s = self.streams[si]
+        now = time.perf_counter()
+        for r in reqs:
+            r.admitted = now
+            r.attempts += 1
+        nbytes = sum(r.nbytes for r in reqs)
+        self.used += nbytes
+        delta, acc, state_off, ks = dfamin.pack_batch(reqs)
+        opt = dfamin.options(closure=closure, max_passes=0 if closure else self.pass_cap,
+                             flags=self.flags)
+        plan = dfamin.BatchPlan(state_off, ks, opt)
+        h_delta = torch.from_numpy(delta).pin_memory()
+        h_acc = torch.from_numpy(acc.view(np.int32)).pin_memory()
+        host_out = torch.empty(plan.states, dtype=torch.int32, pin_memory=True)
+        host_per = torch.empty((3, plan.count), dtype=torch.int32, pin_memory=True)
+        ev_start = torch.cuda.Event(enable_timing=True)
+        ev_end = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            ev_start.record(s)
+            d_delta = torch.empty(delta.size, dtype=torch.int32, device=self.device)
+            d_acc = torch.empty(acc.size, dtype=torch.int32, device=self.device)
+            d_delta.copy_(h_delta, non_blocking=True)
+            d_acc.copy_(h_acc, non_blocking=True)
+            ws = dfamin.Workspace(self.device)
+            out, per = plan.run(d_delta, d_acc, workspace=ws, stream=s)
+            host_out.copy_(out, non_blocking=True)
+            host_per.copy_(per, non_blocking=True)
+            ev_end.record(s)
+        tensors = [h_delta, h_acc, d_delta, d_acc, ws, out, per]
+        self.inflight.append(_Batch(reqs, closure, si, plan, tensors, host_out, host_per,
+                                    state_off, ev_start, ev_end, nbytes))
+        self.stats.batches += 1
+        self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
+
+    def _finish(self, b: _Batch):
+        now = time.perf_counter()
+        per = b.host_per.numpy()
+        out = b.host_out.numpy()
+        self.stats.intervals.append((self._base.elapsed_time(b.ev_start),
+                                     self._base.elapsed_time(b.ev_end)))
+        requeue = []
+        for i, r in enumerate(b.reqs):
+            st = int(per[2, i])
+            if st == dfamin.ENOCONVERGE and not b.closure:
+                r.closure = True                      # deep refinement: rerun on the closure
+                requeue.append(r)
+                self.stats.escalated += 1
+                continue
+            r.status = st
+            r.nblocks = int(per[0, i])
+            r.passes = int(per[1, i])
+            r.out_block = out[b.state_off[i]: b.state_off[i + 1]].copy()
+            r.done = now
+            self.completed.append(r)
+        for r in reversed(requeue):
+            self.pending.appendleft(r)
+        self.used -= b.nbytes
+        self.free.append(b.stream_idx)
+        self.inflight.remove(b)
+        b.plan.close()                                # stream-ordered free: no device sync
+
+    def max_device_overlap(self) -> int:
+        """Largest number of batches whose device intervals (start..end events) overlap."""
+        ev = []
+        for a, z in self.stats.intervals:
+            ev.append((a, 1))
+            ev.append((z, -1))
+        cur = best = 0
+        for _, d in sorted(ev, key=lambda x: (x[0], x[1])):
+            cur += d
+            best = max(best, cur)
+        return best

@@ -1,0 +1,122 @@
+"""The continuous-batching server: every result is identical alone and in the mix (bit-exact,
+as all outputs are integers) and equal to the oracle; batches overlap on the device; admission
+respects the HBM budget; cancellation and a bad request affect nobody else."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_22764_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22764_gb300 import dfamin, serve
+    return dfamin, serve
+
+
+def request_mix(seed=0, count=36, max_n=150_000):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(10 ** rng.uniform(3, np.log10(max_n)))
+        k = int(rng.integers(2, 9))
+        u = rng.random()
+        if i % 9 == 4:
+            out.append(I.path_fib_dfa(4096))                        # deep refinement
+        elif u < 0.5:
+            out.append(I.random_dfa(n, k, 0.5, int(rng.integers(1 << 30))))
+        else:
+            out.append(I.inflated_dfa(max(1, n // 4), k, 4, 0.5, int(rng.integers(1 << 30)),
+                                      permute=False)[0])
+    return out
+
+
+def solo(serve, d):
+    srv = serve.Server(budget_bytes=8 << 30)
+    r = srv.submit(d.n, d.k, d.delta, d.accept)
+    srv.drain()
+    return r
+
+
+def test_alone_and_in_mix_identical(mods):
+    dfamin, serve = mods
+    dfas = request_mix(1)
+    alone = [solo(serve, d) for d in dfas]
+    srv = serve.Server(budget_bytes=8 << 30, streams=4)
+    reqs = []
+    for i, d in enumerate(dfas):                 # arrivals interleaved with scheduling
+        reqs.append(srv.submit(d.n, d.k, d.delta, d.accept))
+        if i % 3 == 2:
+            srv.step()
+    srv.drain()
+    assert srv.stats.escalated >= 1
+    for d, a, m in zip(dfas, alone, reqs):
+        assert a.status == 0 and m.status == 0
+        assert a.nblocks == m.nblocks and a.passes == m.passes
+        assert np.array_equal(a.out_block, m.out_block)
+        want, wn, _ = oracle.moore(d.delta, d.accept, d.n, d.k)
+        assert m.nblocks == wn and np.array_equal(m.out_block, want)
+
+
+def test_batches_overlap_on_device(mods):
+    dfamin, serve = mods
+    from oracle.path_depth import path_passes
+    # plain deep-refinement requests (36,880 rounds each, long on the device, light on the
+    # host) launched one per tick: later batches start while earlier ones still run
+    d = I.path_fib_dfa(65536)
+    srv = serve.Server(budget_bytes=64 << 30, streams=4, pass_cap=100_000)
+    for _ in range(3):
+        srv.submit(d.n, d.k, d.delta, d.accept)
+        srv.step()
+    srv.drain()
+    assert srv.stats.batches == 3 and srv.stats.max_inflight >= 2
+    assert srv.max_device_overlap() >= 2
+    want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+    wp, _ = path_passes(I.fibonacci_word(65536))
+    for r in srv.completed:
+        assert r.status == 0 and r.nblocks == wn and r.passes == wp
+        assert np.array_equal(r.out_block, want)
+
+
+def test_budget_admission_and_rejection(mods):
+    dfamin, serve = mods
+    a = I.random_dfa(300_000, 4, 0.5, 1)
+    b = I.random_dfa(300_000, 4, 0.5, 2)
+    probe = serve.Server(budget_bytes=1 << 40)
+    need = probe.request_bytes(a.n, a.k, True)
+    srv = serve.Server(budget_bytes=int(need * 1.5), streams=4)
+    ra = srv.submit(a.n, a.k, a.delta, a.accept)
+    rb = srv.submit(b.n, b.k, b.delta, b.accept)
+    srv.step()
+    assert len(srv.inflight) == 1 and srv.used <= srv.budget and rb.admitted is None
+    srv.drain()
+    assert ra.status == 0 and rb.status == 0 and rb.admitted >= ra.done - 1e-3
+    huge = I.random_dfa(2_000_000, 8, 0.5, 3)
+    rh = srv.submit(huge.n, huge.k, huge.delta, huge.accept)
+    assert rh.status == dfamin.ENOMEM and srv.stats.rejected == 1
+
+
+def test_cancel_and_bad_request_are_isolated(mods):
+    dfamin, serve = mods
+    dfas = request_mix(2, count=10, max_n=50_000)
+    bad = I.random_dfa(20_000, 3, 0.5, 9)
+    bad_delta = bad.delta.copy()
+    bad_delta[5] = -4
+    srv = serve.Server(budget_bytes=8 << 30)
+    reqs = [srv.submit(d.n, d.k, d.delta, d.accept) for d in dfas[:5]]
+    rbad = srv.submit(bad.n, bad.k, bad_delta, bad.accept)
+    rc = srv.submit(dfas[5].n, dfas[5].k, dfas[5].delta, dfas[5].accept)
+    assert srv.cancel(rc)
+    reqs += [srv.submit(d.n, d.k, d.delta, d.accept) for d in dfas[6:]]
+    srv.drain()
+    assert rbad.status == dfamin.EINVAL and rc.cancelled and rc.out_block is None
+    for r, d in zip(reqs, dfas[:5] + dfas[6:]):
+        want, wn, _ = oracle.moore(d.delta, d.accept, d.n, d.k)
+        assert r.status == 0 and r.nblocks == wn and np.array_equal(r.out_block, want)
