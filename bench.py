@@ -203,6 +203,7 @@ def main():
 
     import torch
     from paper_2410_22764_gb300 import dfamin
+    from paper_2410_22764_gb300.multi import aggregate
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -253,13 +254,10 @@ def main():
         pg.barrier()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
     visits_per_step = n * k * passes
-    value = world * visits_per_step * args.steps / (total_ms / 1e3)
+    # replicas: the slowest rank's time, the edge visits of every rank
+    total_ms, total_visits = aggregate(sum(step_ms), float(visits_per_step * args.steps), pg, dev)
+    value = total_visits / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
     # end to end through the public call from pinned host buffers
@@ -282,12 +280,9 @@ def main():
             stream.synchronize()
             if i > 0:                          # first iteration is a warm-up
                 e_ms += e_start.elapsed_time(e_end)
-    if pg:
-        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_ms, e_visits = aggregate(e_ms, float(visits_per_step * args.e2e_steps), pg, dev)
     assert int(h_sc[0]) == nblocks and int(h_sc[2]) == 0
-    e2e_value = world * visits_per_step * args.e2e_steps / (e_ms / 1e3)
+    e2e_value = e_visits / (e_ms / 1e3)
 
     peaks, peak_kind = measured_peaks()
     alg_bytes = passes * 4 * n * (k + 2)           # per launch: passes x 4n(k+2)

@@ -120,7 +120,7 @@ using namespace dfamin_dev;
 
 namespace {
 
-// Workspace of one DFA: [control | per-CTA counts | identity flags | trace | DFA arrays].
+// Workspace of one DFA: [control | per-CTA counts | identity flags | DFA arrays | trace].
 struct Layout {
     size_t ctrl, cta_cnt, nonid, zero_end;  // [ctrl .. zero_end) is zeroed per launch
     size_t trace, dfa, total;
@@ -136,11 +136,11 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
     L.cta_cnt = off; off = align_up(off + sizeof(int32_t) * kMaxCtas, A);
     L.nonid = off; off = align_up(off + sizeof(int32_t) * (size_t)(k > 0 ? k : 1), A);
     L.zero_end = off;
-    L.trace = off;
-    if (o.flags & DFAMIN_FLAG_TRACE) off += DFAMIN_TRACE_BYTES;
     L.dfa = off;
     L.d = make_dfa_layout(n, k, o.closure == DFAMIN_CLOSURE_ON, true);
     off += L.d.total;
+    L.trace = off;                          // the trace is the workspace's last bytes
+    if (o.flags & DFAMIN_FLAG_TRACE) off += DFAMIN_TRACE_BYTES;
     L.total = off;
     return L;
 }

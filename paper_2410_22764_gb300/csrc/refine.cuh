@@ -164,6 +164,25 @@ static __device__ __forceinline__ int is_accepting(const Job& J, int s)
     return (int)((__ldg(&J.accept[b >> 5]) >> (b & 31)) & 1u);
 }
 
+// Block-id loads.  block[] is written in the kernel (so no non-coherent loads); its random
+// gathers are the hot traffic of every round, and with DFAMIN_GATHER_KEEP they carry an L2
+// evict-last policy so that the streamed delta rows do not push block ids out of L2.
+#ifndef DFAMIN_GATHER_KEEP
+#define DFAMIN_GATHER_KEEP 1
+#endif
+static __device__ __forceinline__ int ld_blk(const int32_t* p)
+{
+#if DFAMIN_GATHER_KEEP
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    int v;
+    asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+#else
+    return __ldcg(p);
+#endif
+}
+
 // Successor of s under signature column c: the k letters, then the closure columns.
 static __device__ __forceinline__ int succ_col(const Job& J, int s, int c)
 {
@@ -396,7 +415,7 @@ static __device__ __forceinline__ void row_chunk(const Job& J, int s, int head, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int i = 4 * v + j;
-        x[j] = (i == 0) ? head : (i <= ncols ? __ldcg(&J.block[succ_col(J, s, i - 1)]) : 0);
+        x[j] = (i == 0) ? head : (i <= ncols ? ld_blk(&J.block[succ_col(J, s, i - 1)]) : 0);
     }
 }
 
@@ -520,7 +539,7 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
     int nL = 0, nr[KC];
     {
         const int s = c0 + threadIdx.x;
-        if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
+        if (s < c1) { nL = ld_blk(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
     }
     for (int base = c0; base < c1; base += blockDim.x) {
         const int s = base + threadIdx.x;
@@ -530,11 +549,11 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         for (int c = 0; c < KC; ++c) r[c] = nr[c];
         if (DFAMIN_PREFETCH) {
             if (s + (int)blockDim.x < c1) {
-                nL = __ldcg(&J.block[s + blockDim.x]);
+                nL = ld_blk(&J.block[s + blockDim.x]);
                 load_succ<KC>(J.delta, s + blockDim.x, nr);
             }
         } else if (s < c1) {
-            L = __ldcg(&J.block[s]);
+            L = ld_blk(&J.block[s]);
             load_succ<KC>(J.delta, s, r);
         }
         bool moved = false, fill = false, lfill = false;
@@ -552,7 +571,7 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
             }
             row[0] = L;
 #pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+            for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
 #pragma unroll
             for (int c = KC + 1; c < SS; ++c) row[c] = 0;
             bool same = true;
@@ -626,7 +645,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
             int row[SS];
             row[0] = s;
 #pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+            for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
 #pragma unroll
             for (int c = KC + 1; c < SS; ++c) row[c] = 0;
             store_row<SS>(J.sig, s, row);
@@ -655,7 +674,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
         int nL = 0, nr[KC];
         {
             const int s = c0 + threadIdx.x;
-            if (s < c1) { nL = __ldcg(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
+            if (s < c1) { nL = ld_blk(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
         }
         for (int base = c0; base < c1; base += blockDim.x) {
             const int s = base + threadIdx.x;
@@ -665,11 +684,11 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             for (int c = 0; c < KC; ++c) r[c] = nr[c];
             if (DFAMIN_PREFETCH) {
                 if (s + (int)blockDim.x < c1) {
-                    nL = __ldcg(&J.block[s + blockDim.x]);
+                    nL = ld_blk(&J.block[s + blockDim.x]);
                     load_succ<KC>(J.delta, s + blockDim.x, nr);
                 }
             } else if (s < c1) {
-                L = __ldcg(&J.block[s]);
+                L = ld_blk(&J.block[s]);
                 load_succ<KC>(J.delta, s, r);
             }
             bool moved = false;
@@ -680,7 +699,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                 int row[SS];
                 row[0] = L;
 #pragma unroll
-                for (int c = 0; c < KC; ++c) row[1 + c] = __ldcg(&J.block[r[c]]);
+                for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
 #pragma unroll
                 for (int c = KC + 1; c < SS; ++c) row[c] = 0;
                 bool same = true;
@@ -704,7 +723,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             bool moved = false;
             uint32_t slot = 0;
             if (s < c1) {
-                const int L = __ldcg(&J.block[s]);
+                const int L = ld_blk(&J.block[s]);
                 if (L != s) {
                     const int4* lrow =
                         reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
@@ -997,7 +1016,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         // ---- canonical ids: rank of each leader among leaders, in state order
         int heads = 0;
         for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
-            heads += (__ldcg(&J.block[s]) == s);
+            heads += (ld_blk(&J.block[s]) == s);
         heads = cta_sum(heads);
         if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
         if (!team_barrier(ts)) goto done;
@@ -1012,7 +1031,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         }
         for (int base = c0; base < c1; base += blockDim.x) {
             const int s = base + threadIdx.x;
-            const int head = (s < c1) && (__ldcg(&J.block[s]) == s);
+            const int head = (s < c1) && (ld_blk(&J.block[s]) == s);
             int tile_total;
             const int pre = cta_scan_flag(head, &tile_total);
             if (head) J.out_block[s] = offset + pre;
@@ -1020,7 +1039,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         }
         if (!team_barrier(ts)) goto done;
         for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-            const int L = __ldcg(&J.block[s]);
+            const int L = ld_blk(&J.block[s]);
             if (L != s) J.out_block[s] = __ldcg(&J.out_block[L]);
         }
         if (rank == T - 1 && threadIdx.x == 0) write_outputs(J, total, passes);
