@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--workload", default="config2",
                     choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve"])
     ap.add_argument("--requests", type=int, default=600)
+    ap.add_argument("--path-variant", default="both", choices=["both", "closure", "plain"])
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

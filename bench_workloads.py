@@ -83,11 +83,19 @@ def run_random1k(args):
 
 def run_path(args):
     d = I.path_fib_dfa(1 << 20)
-    clo = single(args, "closure", d, closure=True, steps=10)
-    plain = single(args, "plain", d, steps=2, warmup=3)
+    extra = {}
+    clo = plain = None
+    if args.path_variant in ("both", "closure"):
+        clo = single(args, "closure", d, closure=True, steps=10)
+        extra["closure"] = clo
+    if args.path_variant in ("both", "plain"):
+        plain = single(args, "plain", d, steps=2, warmup=3)
+        extra["plain"] = plain
+    if clo and plain:
+        extra["speedup_closure_vs_plain"] = plain["ms"] / clo["ms"]
+    main = clo or plain
     _line("path DFA n=2^20 k=2, Fibonacci acceptance: closure (Alg. transPR) vs plain rounds",
-          1e3 / clo["ms"], "minimizations/s", clo["ms"], 10, 3,
-          {"closure": clo, "plain": plain, "speedup_closure_vs_plain": plain["ms"] / clo["ms"]})
+          1e3 / main["ms"], "minimizations/s", main["ms"], main["steps"], 3, extra)
 
 
 def _batch_inputs(kind):

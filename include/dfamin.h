@@ -148,9 +148,10 @@ typedef struct dfamin_batch_plan_s *dfamin_batch_plan;
 
 dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t *state_off, const int32_t *k,
                                        const dfamin_options *opt, dfamin_batch_plan *plan);
-/* Destroy only after every launch that used the plan has completed.  Plan creation and
- * destruction use stream-ordered allocation on a library stream: they never wait for work on
- * other streams. */
+/* Plan creation and destruction use stream-ordered allocation on a library stream and never
+ * wait for work on other streams.  Destroying a plan releases its device table after the most
+ * recent launch that used it has completed (in stream order); a caller that launches one plan
+ * on several streams at once must let those launches complete before destroying it. */
 dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan);
 
 /* Bytes of device workspace a launch with this plan needs (caller-owned, 256-byte aligned). */

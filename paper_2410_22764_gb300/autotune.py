@@ -1,0 +1,152 @@
+"""Autotuner for the schedule knobs of the library.
+
+The knobs change no result, only speed:
+  * single DFAs: the grid of the multi-CTA kernel (``ctas``) and the size limit of the one-CTA
+    shared-memory kernel (``smem_states``);
+  * batches: the one-CTA limit (``smem_states``), the states per CTA when sizing a team
+    (``team_states``) and a cap on the grid (``ctas``).
+Regrouping uses the hash table with full-row verification throughout (there is no second
+regrouping algorithm to choose from).
+
+Candidates are timed on the device (CUDA events, median of a few runs after warm-up) and the
+fastest is stored in a JSON cache keyed by GPU name and a shape bucket, so later calls with a
+similar shape reuse it.  The timing function can be replaced (tests use a fake one).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+import threading
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("DFAMIN_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "dfamin", "tune.json"))
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path: str, data: dict):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def single_key(gpu: str, n: int, k: int, closure: bool) -> str:
+    return f"{gpu}|single|n2^{round(math.log2(max(n, 1)))}|k{k}|c{int(closure)}"
+
+
+def batch_key(gpu: str, ns, ks, closure: bool) -> str:
+    count = len(ns)
+    trans = sum(int(a) * int(b) for a, b in zip(ns, ks))
+    meank = sum(int(b) for b in ks) / max(count, 1)
+    return (f"{gpu}|batch|count2^{round(math.log2(max(count, 1)))}"
+            f"|t2^{round(math.log2(max(trans, 1)))}|k{round(meank)}|c{int(closure)}")
+
+
+def single_candidates(n: int, sms: int) -> list[dict]:
+    cands = [{"ctas": c * sms} for c in (1, 2, 3, 4)]
+    if n <= 8192:
+        cands += [{"smem_states": max(n, 1)}, {"smem_states": 1}]
+    return cands
+
+
+def batch_candidates(sms: int) -> list[dict]:
+    out = []
+    for small in (512, 2048, 4096):
+        for team in (4096, 16384, 65536):
+            out.append({"smem_states": small, "team_states": team})
+    out.append({"smem_states": 2048, "team_states": 16384, "ctas": 2 * sms})
+    return out
+
+
+def choose(key: str, candidates: list[dict], measure, path: str | None = None,
+           retune: bool = False) -> tuple[dict, dict]:
+    """Return (best candidate, {candidate-json: ms}) for `key`, from the cache or by calling
+    measure(candidate) -> milliseconds on every candidate (then cached)."""
+    path = path or cache_path()
+    with _lock:
+        data = _load(path)
+        if not retune and key in data:
+            return data[key]["best"], data[key]["timings"]
+    timings = {}
+    for c in candidates:
+        timings[json.dumps(c, sort_keys=True)] = float(measure(c))
+    best = json.loads(min(timings, key=timings.get))
+    with _lock:
+        data = _load(path)
+        data[key] = {"best": best, "timings": timings}
+        _store(path, data)
+    return best, timings
+
+
+# ------------------------------------------------------------------------------------------
+# device measurement
+# ------------------------------------------------------------------------------------------
+def _gpu_name_and_sms():
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return p.name, p.multi_processor_count
+
+
+def _time_ms(fn, warmup=2, reps=3) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def tune_single(n: int, k: int, delta, accept, closure: bool = False, retune: bool = False,
+                path: str | None = None):
+    """Tuned options for one DFA (device tensors delta, accept)."""
+    from . import dfamin
+    gpu, sms = _gpu_name_and_sms()
+    ws = dfamin.Workspace()
+
+    def measure(c):
+        opt = dfamin.options(closure=closure, **c)
+        return _time_ms(lambda: dfamin.minimize_ex(n, k, delta, accept, opt=opt, workspace=ws))
+    best, timings = choose(single_key(gpu, n, k, closure), single_candidates(n, sms), measure,
+                           path, retune)
+    return dfamin.options(closure=closure, **best), timings
+
+
+def tune_batch(state_off, ks, delta, accept, closure: bool = False, retune: bool = False,
+               path: str | None = None):
+    """Tuned options for a batch (host state_off / ks, device delta / accept)."""
+    import numpy as np
+    from . import dfamin
+    gpu, sms = _gpu_name_and_sms()
+    ns = np.diff(np.asarray(state_off, dtype=np.int64))
+    ws = dfamin.Workspace()
+
+    def measure(c):
+        plan = dfamin.BatchPlan(state_off, ks, dfamin.options(closure=closure, **c))
+        try:
+            return _time_ms(lambda: plan.run(delta, accept, workspace=ws))
+        finally:
+            plan.close()
+    best, timings = choose(batch_key(gpu, ns.tolist(), list(ks), closure), batch_candidates(sms),
+                           measure, path, retune)
+    return dfamin.options(closure=closure, **best), timings

@@ -168,6 +168,7 @@ struct dfamin_batch_plan_s {
     dfamin_options opt{};
     std::vector<BatchDesc> desc;   // ticket order
     BatchDesc* d_desc = nullptr;   // device copy, owned
+    cudaEvent_t last_launch = nullptr;  // recorded on the stream of every launch
     int64_t tickets = 0;
     int grid = 0;
     size_t dsmem = 0;
@@ -335,8 +336,14 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
         delete P;
         return st;
     }
+    if (!cuda_ok(cudaEventCreateWithFlags(&P->last_launch, cudaEventDisableTiming),
+                 "cudaEventCreate(plan)")) {
+        delete P;
+        return DFAMIN_ECUDA;
+    }
     if (!cuda_ok(cudaMallocAsync((void**)&P->d_desc, sizeof(BatchDesc) * (size_t)count, ps),
                  "cudaMallocAsync(plan)")) {
+        cudaEventDestroy(P->last_launch);
         delete P;
         return DFAMIN_ENOMEM;
     }
@@ -345,6 +352,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
                  "cudaMemcpyAsync(plan)") ||
         !cuda_ok(cudaStreamSynchronize(ps), "cudaStreamSynchronize(plan)")) {
         cudaFreeAsync(P->d_desc, ps);
+        cudaEventDestroy(P->last_launch);
         delete P;
         return DFAMIN_ECUDA;
     }
@@ -356,9 +364,15 @@ DFAMIN_API dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan)
 {
     if (!plan) return DFAMIN_EINVAL;
     if (plan->d_desc) {
+        // the table is freed in stream order after the last launch that used the plan (even if
+        // that launch is still running), without blocking the host
         cudaStream_t ps = nullptr;
-        if (plan_stream(plan->dev, &ps) == DFAMIN_OK) cudaFreeAsync(plan->d_desc, ps);
+        if (plan_stream(plan->dev, &ps) == DFAMIN_OK) {
+            if (plan->last_launch) cudaStreamWaitEvent(ps, plan->last_launch, 0);
+            cudaFreeAsync(plan->d_desc, ps);
+        }
     }
+    if (plan->last_launch) cudaEventDestroy(plan->last_launch);
     delete plan;
     return DFAMIN_OK;
 }
@@ -422,6 +436,8 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
                                              dim3(kTeamThreads), args, plan->dsmem,
                                              (cudaStream_t)stream),
                  "batch_kernel cooperative launch"))
+        return DFAMIN_ECUDA;
+    if (!cuda_ok(cudaEventRecord(plan->last_launch, (cudaStream_t)stream), "cudaEventRecord(plan)"))
         return DFAMIN_ECUDA;
     return DFAMIN_OK;
 }

@@ -156,3 +156,23 @@ def test_batch_cuda_graph_replay(dm):
         for i, (b, nb, ps) in enumerate(want):
             assert p[2, i] == 0 and p[0, i] == nb and p[1, i] == ps
             assert np.array_equal(o[i], b)
+
+
+def test_plan_destroyed_right_after_launch(dm):
+    # a plan released while its launch still runs (a Python temporary) must not free the
+    # descriptor table under the running kernel: the free waits for the launch in stream order
+    dfas = mixed_batch(9, count=40, max_n=60000)
+    want = oracle_results(dfas)
+    delta, acc, state_off, ks = dm.pack_batch(dfas)
+    dd = torch.from_numpy(delta).cuda()
+    aa = torch.from_numpy(acc.view(np.int32)).cuda()
+    results = []
+    for _ in range(3):
+        out, per = dm.BatchPlan(state_off, ks, dm.options()).run(dd, aa)
+        results.append((out, per))
+    torch.cuda.synchronize()
+    for out, per in results:
+        o, p = np.split(out.cpu().numpy(), state_off[1:-1]), per.cpu().numpy()
+        for i, (b, nb, ps) in enumerate(want):
+            assert p[2, i] == 0 and p[0, i] == nb and p[1, i] == ps
+            assert np.array_equal(o[i], b)
