@@ -50,7 +50,7 @@ constexpr int kThreads = 256;             // threads per CTA of the one-CTA kern
 #define DFAMIN_PREFETCH 1                 // load the next state's block id and row ahead
 #endif
 #ifndef DFAMIN_SLOT_CACHE
-#define DFAMIN_SLOT_CACHE 512             // per-CTA group-cache entries (rows of <= 8 ints)
+#define DFAMIN_SLOT_CACHE 128             // per-CTA group-cache entries (rows of <= 8 ints)
 #endif
 constexpr int kTeamThreads = DFAMIN_TEAM_THREADS;
 constexpr int kMaxCtas = 8192;            // capacity of the per-CTA count array
@@ -261,6 +261,34 @@ static __device__ int cta_scan_flag(int flag, int* total)
     return base + in_warp;
 }
 
+// Exclusive prefix of an int over the CTA's threads; *total receives the CTA sum.  Must be
+// called by all threads of the CTA.
+static __device__ int cta_scan_count(int v, int* total)
+{
+    __shared__ int s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nwarps ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nwarps) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int base = warp ? s_warp[warp - 1] : 0;
+    *total = s_warp[nwarps - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
 static __device__ int cta_sum(int v)
 {
     __shared__ int s_red[32];
@@ -356,6 +384,19 @@ static __device__ __forceinline__ void load_succ(const int32_t* __restrict__ del
     }
 }
 
+// Round 1 reads every state's row (leaders in phase A, the others in phase B), so the range
+// check of delta is done there, on rows already in registers, instead of in a separate scan:
+// an entry outside [0, n) sets DFAMIN_EINVAL and is never used as an address.
+template <int KC>
+__device__ __forceinline__ bool row_ok(const Job& J, const int (&r)[KC])
+{
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) ok &= (unsigned)r[c] < (unsigned)J.n;
+    if (!ok) set_status(J.ctrl, DFAMIN_EINVAL);
+    return ok;
+}
+
 template <int KC>
 struct RowOf {
     static constexpr int SS = (KC + 1 + 3) / 4 * 4;
@@ -415,7 +456,12 @@ static __device__ __forceinline__ void row_chunk(const Job& J, int s, int head, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int i = 4 * v + j;
-        x[j] = (i == 0) ? head : (i <= ncols ? ld_blk(&J.block[succ_col(J, s, i - 1)]) : 0);
+        int t = 0;
+        if (i >= 1 && i <= ncols) {
+            t = succ_col(J, s, i - 1);
+            if ((unsigned)t >= (unsigned)J.n) { set_status(J.ctrl, DFAMIN_EINVAL); t = 0; }
+        }
+        x[j] = (i == 0) ? head : (i <= ncols ? ld_blk(&J.block[t]) : 0);
     }
 }
 
@@ -496,8 +542,14 @@ static __device__ __forceinline__ void append_moved(const Job& J, int c0, bool m
 // that state, so it needs neither the table nor an atomicMin.
 // ------------------------------------------------------------------------------------------
 constexpr uint32_t kCached = 0x80000000u;  // list slot flag: the low bits index the group cache
-constexpr int kCacheMaxBlocks = 4096;    // rounds that start with at most this many blocks
-constexpr int kLeaderCache = 256;        // leader rows, direct-mapped by leader id
+#ifndef DFAMIN_CACHE_MAX_BLOCKS
+#define DFAMIN_CACHE_MAX_BLOCKS 4096
+#endif
+constexpr int kCacheMaxBlocks = DFAMIN_CACHE_MAX_BLOCKS;  // rounds starting with at most this many blocks
+#ifndef DFAMIN_LEADER_CACHE
+#define DFAMIN_LEADER_CACHE 64
+#endif
+constexpr int kLeaderCache = DFAMIN_LEADER_CACHE;  // leader rows, direct-mapped by leader id
 
 template <int SS>
 struct CtaCache {
@@ -560,7 +612,7 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         uint32_t slot = 0;
         uint64_t h = 0;
         int row[SS], lr[SS];
-        if (s < c1 && L != s) {
+        if (s < c1 && L != s && row_ok<KC>(J, r)) {
             const int li = L & (kLeaderCache - 1);
             if (C.lkey[li] == L) {
 #pragma unroll
@@ -642,6 +694,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                 ns = __ldcg(&J.lead[i + stride]);
                 load_succ<KC>(J.delta, ns, nr);
             }
+            if (!row_ok<KC>(J, r)) continue;
             int row[SS];
             row[0] = s;
 #pragma unroll
@@ -693,7 +746,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             }
             bool moved = false;
             uint32_t slot = 0;
-            if (s < c1 && L != s) {
+            if (s < c1 && L != s && row_ok<KC>(J, r)) {
                 int lr[SS];
                 load_row<SS>(J.sig, L, lr);
                 int row[SS];
@@ -808,7 +861,9 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     {
         bool bad = false;
         const int64_t r0 = (int64_t)c0 * k, r1 = (int64_t)c1 * k;
-        if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
+        if (!closure && n > 2) {
+            // validated in round 1 (row_ok / row_chunk)
+        } else if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
             const int64_t v0 = r0 / 4, v1 = r1 / 4;   // r0 is a multiple of 4 (chunk % 32 == 0)
             const int4* d4 = reinterpret_cast<const int4*>(J.delta);
             for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
@@ -958,14 +1013,24 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                 cache.gmin[ci] = (int)ld_relaxed_u32(&J.table[cache.gslot[ci]]);
                         __syncthreads();
                     }
+                    // software pipeline: the next entry's (state, slot) is loaded ahead
+                    int ns = 0;
+                    uint32_t nslot = 0;
+                    if ((int)threadIdx.x < cnt) {
+                        ns = __ldcs(&J.lst_s[c0 + threadIdx.x]);
+                        nslot = __ldcs(&J.lst_slot[c0 + threadIdx.x]);
+                    }
                     for (int b = 0; b < cnt; b += blockDim.x) {
                         const int i = b + threadIdx.x;
+                        const int s = ns;
+                        const uint32_t slot = nslot;
+                        if (i + (int)blockDim.x < cnt) {
+                            ns = __ldcs(&J.lst_s[c0 + i + blockDim.x]);
+                            nslot = __ldcs(&J.lst_slot[c0 + i + blockDim.x]);
+                        }
                         bool lead = false;
                         uint32_t gs = 0;
-                        int s = 0;
                         if (i < cnt) {
-                            s = J.lst_s[c0 + i];
-                            const uint32_t slot = J.lst_slot[c0 + i];
                             int m;
                             if (use_cache && (slot & kCached)) {
                                 const int ci = (int)(slot & ~kCached);
@@ -1013,10 +1078,17 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         }
         if (ld_volatile(&J.ctrl->status) != 0) goto done;
 
-        // ---- canonical ids: rank of each leader among leaders, in state order
+        // ---- canonical ids: rank of each leader among leaders, in state order.  Chunks start
+        //      at multiples of 32 states, so block[] is read as int4 (4 states per thread).
         int heads = 0;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
-            heads += (ld_blk(&J.block[s]) == s);
+        for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += 4 * blockDim.x) {
+            if (s + 3 < c1) {
+                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
+                heads += (b.x == s) + (b.y == s + 1) + (b.z == s + 2) + (b.w == s + 3);
+            } else {
+                for (int j = s; j < c1; ++j) heads += (ld_blk(&J.block[j]) == j);
+            }
+        }
         heads = cta_sum(heads);
         if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
         if (!team_barrier(ts)) goto done;
@@ -1029,18 +1101,41 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             for (int r = threadIdx.x; r < T; r += blockDim.x) total += __ldcg(&J.cta_cnt[r]);
             total = cta_sum(total);
         }
-        for (int base = c0; base < c1; base += blockDim.x) {
-            const int s = base + threadIdx.x;
-            const int head = (s < c1) && (ld_blk(&J.block[s]) == s);
+        for (int base = c0; base < c1; base += 4 * blockDim.x) {
+            const int s = base + 4 * (int)threadIdx.x;
+            int f[4] = {0, 0, 0, 0};
+            if (s + 3 < c1) {
+                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
+                f[0] = b.x == s; f[1] = b.y == s + 1; f[2] = b.z == s + 2; f[3] = b.w == s + 3;
+            } else {
+                for (int j = 0; j < 4; ++j) f[j] = (s + j < c1) && (ld_blk(&J.block[s + j]) == s + j);
+            }
             int tile_total;
-            const int pre = cta_scan_flag(head, &tile_total);
-            if (head) J.out_block[s] = offset + pre;
+            int pre = offset + cta_scan_count(f[0] + f[1] + f[2] + f[3], &tile_total);
+            for (int j = 0; j < 4; ++j)
+                if (f[j]) J.out_block[s + j] = pre++;
             offset += tile_total;
         }
         if (!team_barrier(ts)) goto done;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-            const int L = ld_blk(&J.block[s]);
-            if (L != s) J.out_block[s] = __ldcg(&J.out_block[L]);
+        // out_block is the caller's array (in a batch: at the DFA's offset), so its int4 access
+        // is used only when it is 16-byte aligned; block[] is in the workspace (aligned)
+        const bool out_aligned = ((uintptr_t)J.out_block & 15u) == 0;
+        for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += 4 * blockDim.x) {
+            if (s + 3 < c1 && out_aligned) {
+                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
+                const int4 o = __ldcg(reinterpret_cast<const int4*>(J.out_block + s));
+                int4 r;
+                r.x = b.x == s ? o.x : __ldcg(&J.out_block[b.x]);
+                r.y = b.y == s + 1 ? o.y : __ldcg(&J.out_block[b.y]);
+                r.z = b.z == s + 2 ? o.z : __ldcg(&J.out_block[b.z]);
+                r.w = b.w == s + 3 ? o.w : __ldcg(&J.out_block[b.w]);
+                *reinterpret_cast<int4*>(J.out_block + s) = r;
+            } else {
+                for (int j = s; j < c1; ++j) {
+                    const int L = ld_blk(&J.block[j]);
+                    if (L != j) J.out_block[j] = __ldcg(&J.out_block[L]);
+                }
+            }
         }
         if (rank == T - 1 && threadIdx.x == 0) write_outputs(J, total, passes);
         if (J.trace) {                                // J.trace is uniform over the team
