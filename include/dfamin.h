@@ -58,6 +58,15 @@ typedef enum {
 #define DFAMIN_CLOSURE_OFF 0   /* plain refinement on A (Alg. sortPR semantics) */
 #define DFAMIN_CLOSURE_ON 1    /* refinement on the closed DFA A' of Alg. transPR */
 
+/* algorithm */
+#define DFAMIN_ALG_SIGNATURE 0 /* signature refinement, Alg. sortPR (Sec. 3.3): a block may split
+                                  into many blocks per round (default) */
+#define DFAMIN_ALG_LEADER 1    /* leader election, Alg. 2 naivePR (Sec. 3.2): per round, the states
+                                  of a block that differ from its leader move, together, to one new
+                                  block led by the smallest of them; rounds run until one changes
+                                  nothing (the final, unchanged round is counted).  With the closure
+                                  this is transPR exactly as Alg. transPR runs it (naivePR on A') */
+
 /* flags */
 #define DFAMIN_FLAG_KEEP_IDENTITY 1u  /* closure: also close letters whose delta is the identity
                                          (by default their columns, all equal to the identity,
@@ -82,7 +91,8 @@ typedef struct {
     int32_t ctas;        /* 0 = automatic; otherwise number of CTAs for one DFA (tuning) */
     int32_t smem_states; /* 0 = automatic; largest n solved by one CTA in shared memory */
     int32_t team_states; /* batches: 0 = automatic; states per CTA when sizing a DFA's team */
-    int32_t reserved[2]; /* must be 0 */
+    int32_t algorithm;   /* DFAMIN_ALG_SIGNATURE (default) or DFAMIN_ALG_LEADER */
+    int32_t reserved;    /* must be 0 */
 } dfamin_options;
 
 /* Fills *opt with the defaults (closure off, automatic tuning). */

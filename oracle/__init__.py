@@ -10,6 +10,7 @@ Each function follows one passage of the paper:
 * :func:`hopcroft`   - Hopcroft's quasi-linear refinement named in Sec. 1.
 * :func:`tablefill`  - pairwise marking, the sequential meaning of Alg. 1 ``trans`` (Sec. 3.1).
 * :func:`closure`    - the per-letter partial transitive closure of Alg. transPR (Sec. 3.4).
+* :func:`naive`      - leader-election refinement, Alg. 2 naivePR (Sec. 3.2).
 * :func:`canonical`  - canonical relabelling (block id = rank of the block's smallest state).
 * :func:`check_stable` - congruence property check that holds at any size.
 
@@ -60,6 +61,8 @@ def _load():
             lib.oracle_closure_levels.restype = i32
             lib.oracle_closure.argtypes = [i32, i32, p, p]
             lib.oracle_check_stable.argtypes = [i32, i32, p, p, p]
+            lib.oracle_naive.argtypes = [i32, i32, p, p, i32, p, p, p]
+            lib.oracle_naive.restype = ctypes.c_int
             for f in (lib.oracle_canonical, lib.oracle_moore, lib.oracle_hopcroft,
                       lib.oracle_tablefill, lib.oracle_closure, lib.oracle_check_stable):
                 f.restype = ctypes.c_int
@@ -108,6 +111,20 @@ def moore(delta, accept, n: int, k: int, max_passes: int = 0, partial: bool = Fa
     if rc not in (0, ENOCONVERGE):
         raise ValueError(f"oracle_moore failed ({rc})")
     return out, nb.value, ps.value
+
+
+def naive(delta, accept, n: int, k: int, max_iters: int = 0):
+    """Alg. 2 naivePR (smallest writer wins each election); returns (block, nblocks, iters)."""
+    delta, accept = _prep(delta, accept, n, k)
+    out = np.empty(n, np.int32)
+    nb, it = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = _load().oracle_naive(n, k, _ptr(delta), _ptr(accept), max_iters, _ptr(out),
+                              ctypes.byref(nb), ctypes.byref(it))
+    if rc == ENOCONVERGE:
+        raise RuntimeError(f"oracle_naive hit max_iters={max_iters}")
+    if rc != 0:
+        raise ValueError(f"oracle_naive failed ({rc})")
+    return out, nb.value, it.value
 
 
 def hopcroft(delta, accept, n: int, k: int):

@@ -23,6 +23,7 @@
  *   oracle_hopcroft    Hopcroft's splitter-worklist refinement (Sec. 1, [Hopcroft 1971])
  *   oracle_tablefill   pairwise marking: the sequential meaning of Alg. 1 "trans" (Sec. 3.1)
  *   oracle_closure     the per-letter partial transitive closure of Alg. transPR (Sec. 3.4)
+ *   oracle_naive       leader-election refinement, the steps of Alg. 2 naivePR (Sec. 3.2)
  *   oracle_check_stable  property check: refines {F, Q\F} and is stable under delta
  *
  * Every routine returns 0 on success and a negative value on bad arguments or allocation
@@ -500,4 +501,88 @@ int oracle_check_stable(int32_t n, int32_t k, const int32_t *delta, const uint32
     }
     free(rep);
     return ok;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Leader-election refinement, the steps of Alg. 2 naivePR (Sec. 3.2):
+ *   block[q] := (q in F ? q_f : q_n)                      initial leaders
+ *   while not stable:
+ *     stable := true
+ *     for all (q, a): if block[delta(q,a)] != block[delta(block[q], a)]:
+ *         new_leader[block[q]] := q                         leader election
+ *     for all (q, a): if block[delta(q,a)] != block[delta(block[q], a)]:
+ *         block[q] := new_leader[block[q]]; stable := false split from the leader
+ * Readings (also in the design notes): the initial leaders are the smallest accepting and the
+ * smallest rejecting state; of the concurrent writes of one election the smallest q wins
+ * (the listing lets any one win); each parallel loop reads block[] as it was before the loop
+ * (synchronous PRAM step).  *iters counts executed while-iterations, the final one that finds
+ * nothing to split included.  max_iters <= 0 means no cap.
+ * ------------------------------------------------------------------------------------------ */
+int oracle_naive(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,
+                 int32_t max_iters, int32_t *out_block, int32_t *nblocks, int32_t *iters)
+{
+    if (n < 1 || k < 0 || (k > 0 && !delta) || !accept || !out_block)
+        return ORACLE_EARG;
+    if (check_delta(n, k, delta) != ORACLE_OK)
+        return ORACLE_EARG;
+    size_t nn = (size_t)n;
+    int32_t *block = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *next = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *new_leader = (int32_t *)malloc(sizeof(int32_t) * nn);
+    uint8_t *differs = (uint8_t *)malloc(nn);
+    if (!block || !next || !new_leader || !differs) {
+        free(block); free(next); free(new_leader); free(differs);
+        return ORACLE_ENOMEM;
+    }
+    int32_t qf = -1, qn = -1;
+    for (int32_t q = 0; q < n; q++) {
+        if (is_accepting(accept, q)) { if (qf < 0) qf = q; }
+        else if (qn < 0) qn = q;
+    }
+    for (int32_t q = 0; q < n; q++)
+        block[q] = is_accepting(accept, q) ? qf : qn;
+    int32_t it = 0;
+    int rc = ORACLE_OK;
+    for (;;) {
+        if (max_iters > 0 && it >= max_iters) {
+            rc = ORACLE_ENOCONVERGE;
+            break;
+        }
+        it++;
+        int stable = 1;
+        for (int32_t q = 0; q < n; q++) {
+            differs[q] = 0;
+            new_leader[q] = -1;
+        }
+        /* election: reads block[] only */
+        for (int32_t q = 0; q < n; q++)
+            for (int32_t a = 0; a < k; a++) {
+                int32_t l = block[q];
+                if (block[delta[(int64_t)q * k + a]] != block[delta[(int64_t)l * k + a]]) {
+                    differs[q] = 1;
+                    if (new_leader[l] < 0 || q < new_leader[l])
+                        new_leader[l] = q;
+                }
+            }
+        /* split: every test reads the block[] of before the loop, then the writes apply */
+        for (int32_t q = 0; q < n; q++)
+            next[q] = differs[q] ? new_leader[block[q]] : block[q];
+        for (int32_t q = 0; q < n; q++) {
+            if (next[q] != block[q])
+                stable = 0;
+            block[q] = next[q];
+        }
+        if (stable)
+            break;
+    }
+    int32_t c = 0;
+    int rc2 = oracle_canonical(n, block, out_block, &c);
+    if (rc == ORACLE_OK)
+        rc = rc2;
+    if (nblocks)
+        *nblocks = c;
+    if (iters)
+        *iters = it;
+    free(block); free(next); free(new_leader); free(differs);
+    return rc;
 }

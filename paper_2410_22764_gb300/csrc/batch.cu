@@ -48,7 +48,7 @@ struct BatchDesc {             // one DFA, in ticket order
     int32_t cta_base;          // first entry of its per-CTA counts
     int32_t nonid_base;        // first entry of its identity-letter flags
     int64_t o_block, o_lst_s, o_lst_slot, o_lst_rst, o_lead, o_lead_slot, o_stg, o_table, o_sig,
-        o_cl, o_cl_letter;
+        o_cl, o_cl_letter, o_naive;
 };
 
 struct BatchArgs {
@@ -67,6 +67,7 @@ struct BatchArgs {
     int32_t* nonid;                // zeroed per launch
     int32_t* cta_cnt;
     uint32_t flags;
+    int32_t algo;
 };
 
 __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
@@ -93,6 +94,8 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.lead = (int32_t*)(r + D.o_lead);
     J.lead_slot = (uint32_t*)(r + D.o_lead_slot);
     J.stg = (int32_t*)(r + D.o_stg);
+    J.naive_new = (int32_t*)(r + D.o_naive);
+    J.algo = A.algo;
     J.table = (uint32_t*)(r + D.o_table);
     J.mask = D.cap - 1;
     J.sig = (int32_t*)(r + D.o_sig);
@@ -251,7 +254,8 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
     size_t dsmem = 0;
     for (int32_t i = 0; i < count; ++i) {
         const int64_t n = state_off[i + 1] - state_off[i];
-        if (n <= small_limit) dsmem = std::max(dsmem, small_smem_bytes((int32_t)n, nullptr));
+        if (n <= small_limit && o.algorithm == DFAMIN_ALG_SIGNATURE)
+            dsmem = std::max(dsmem, small_smem_bytes((int32_t)n, nullptr));
         else dsmem = std::max(dsmem, cache_bytes_for(k[i], closure));
     }
     if (dsmem + 2048 > smem_optin) return DFAMIN_EINVAL;
@@ -292,7 +296,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
         D.n = (int32_t)(state_off[i + 1] - state_off[i]);
         D.k = k[i];
         D.state_off = state_off[i];
-        D.small = D.n <= small_limit ? 1 : 0;
+        D.small = (D.n <= small_limit && o.algorithm == DFAMIN_ALG_SIGNATURE) ? 1 : 0;
         D.team = D.small ? 1
                          : (int32_t)std::min<int64_t>(
                                std::max<int64_t>(1, ((int64_t)D.n + team_states - 1) / team_states),
@@ -324,6 +328,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
         D.o_block = L.block; D.o_lst_s = L.lst_s; D.o_lst_slot = L.lst_slot;
         D.o_lst_rst = L.lst_rst; D.o_lead = L.lead; D.o_lead_slot = L.lead_slot; D.o_stg = L.stg;
         D.o_table = L.table; D.o_sig = L.sig; D.o_cl = L.cl; D.o_cl_letter = L.cl_letter;
+        D.o_naive = L.naive_new;
         off = align_up(off + L.total, A);
     }
     P->ws_bytes = off;
@@ -431,6 +436,7 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
     A.nonid = (int32_t*)(base + plan->off_nonid);
     A.cta_cnt = (int32_t*)(base + plan->off_cta);
     A.flags = plan->opt.flags & ~DFAMIN_FLAG_TRACE;
+    A.algo = plan->opt.algorithm;
     void* args[] = {&A};
     if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(plan->grid),
                                              dim3(kTeamThreads), args, plan->dsmem,

@@ -185,6 +185,7 @@ void bind_dfa_arrays(Job& J, unsigned char* region, const DfaLayout& d)
     J.lead = (int32_t*)(region + d.lead);
     J.lead_slot = (uint32_t*)(region + d.lead_slot);
     J.stg = (int32_t*)(region + d.stg);
+    J.naive_new = (int32_t*)(region + d.naive_new);
     J.table = (uint32_t*)(region + d.table);
     J.mask = d.cap - 1;
     J.sig = (int32_t*)(region + d.sig);
@@ -230,6 +231,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     bind_dfa_arrays(J, base + L.dfa, L.d);
     J.max_passes = o.max_passes > 0 ? o.max_passes : (n < 0x7fffffff ? n + 1 : n);
     J.flags = o.flags;
+    J.algo = o.algorithm;
     J.timeout_ns = kBarrierTimeoutNs;
     if (o.flags & DFAMIN_FLAG_TRACE) {
         J.trace = (long long*)(base + L.trace);
@@ -245,7 +247,8 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     const int small_limit = o.smem_states > 0 ? o.smem_states : 4096;
     uint32_t scap = 0;
     const size_t smem = small_smem_bytes(n, &scap);
-    if (n <= small_limit && n <= kSmallMaxStates && smem + 1024 <= smem_optin) {
+    if (o.algorithm == DFAMIN_ALG_SIGNATURE && n <= small_limit && n <= kSmallMaxStates &&
+        smem + 1024 <= smem_optin) {
         int per_sm = 0;
         st = kernel_ctas_per_sm(dev, (const void*)small_kernel, kThreads, smem, &per_sm);
         if (st != DFAMIN_OK) return st;

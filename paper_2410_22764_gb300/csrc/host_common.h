@@ -35,7 +35,9 @@ inline dfamin_status check_options(const dfamin_options& o)
     if (o.closure != DFAMIN_CLOSURE_OFF && o.closure != DFAMIN_CLOSURE_ON) return DFAMIN_EINVAL;
     if (o.max_passes < 0 || o.ctas < 0 || o.smem_states < 0 || o.team_states < 0)
         return DFAMIN_EINVAL;
-    if (o.reserved[0] || o.reserved[1]) return DFAMIN_EINVAL;
+    if (o.algorithm != DFAMIN_ALG_SIGNATURE && o.algorithm != DFAMIN_ALG_LEADER)
+        return DFAMIN_EINVAL;
+    if (o.reserved) return DFAMIN_EINVAL;
     return DFAMIN_OK;
 }
 
@@ -49,7 +51,8 @@ inline size_t small_smem_bytes(int32_t n, uint32_t* cap_out)
 
 // Per-DFA arrays of the multi-CTA path, as byte offsets from the start of the DFA's region.
 struct DfaLayout {
-    size_t block, lst_s, lst_slot, lst_rst, lead, lead_slot, stg, table, sig, cl, cl_letter;
+    size_t block, lst_s, lst_slot, lst_rst, lead, lead_slot, stg, table, sig, cl, cl_letter,
+        naive_new;
     size_t total;
     uint32_t cap;       // group-table capacity (power of two)
     int levels;         // 1 + floor(log2 n) with the closure, else 1
@@ -74,6 +77,7 @@ inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays
         L.lead = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
         L.lead_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
         L.stg = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
+        L.naive_new = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
         L.table = off; off = align_up(off + sizeof(uint32_t) * (size_t)L.cap, A);
         L.sig = off;
         off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);

@@ -102,6 +102,8 @@ struct Job {
     int64_t timeout_ns;
     long long* trace;                    // phase trace or null
     long long trace_cap;                 // records
+    int32_t algo;                        // DFAMIN_ALG_SIGNATURE or DFAMIN_ALG_LEADER
+    int32_t* naive_new;                  // [n] leader mode: elected new leader per old leader
 };
 
 static __device__ __forceinline__ uint64_t gtimer()
@@ -514,6 +516,17 @@ static __device__ uint32_t insert_row_generic(const Job& J, int s, int head, uin
     return kFail;
 }
 
+// Leader mode (Alg. 2 naivePR): a state that differs from its leader L is elected into the one
+// new block split from L this round; the block's new leader is the smallest such state (the
+// listing lets any concurrent writer win; the smallest makes runs reproducible).  The list
+// entry keeps L, whose election result phase C reads.
+__device__ __forceinline__ uint32_t naive_elect(const Job& J, int s, int L)
+{
+    if ((uint32_t)s < (uint32_t)ld_relaxed_u32((const uint32_t*)&J.naive_new[L]))
+        atomicMin(&J.naive_new[L], s);
+    return (uint32_t)L;
+}
+
 // Appends (s, slot) for the lanes with `moved` set: one shared atomic per warp.
 static __device__ __forceinline__ void append_moved(const Job& J, int c0, bool moved, int s,
                                              uint32_t slot, int* s_cnt)
@@ -758,7 +771,10 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                 bool same = true;
 #pragma unroll
                 for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
-                if (!same) {                          // T(s) != T(leader): regroup
+                if (!same && J.algo == DFAMIN_ALG_LEADER) {
+                    slot = naive_elect(J, s, L);
+                    moved = true;
+                } else if (!same) {                   // T(s) != T(leader): regroup
                     uint64_t h = hash_begin(L);
 #pragma unroll
                     for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
@@ -795,7 +811,10 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                             same = l.x == x[0] && l.y == x[1] && l.z == x[2] && l.w == x[3];
                         }
                     }
-                    if (!same) {
+                    if (!same && J.algo == DFAMIN_ALG_LEADER) {
+                        slot = naive_elect(J, s, L);
+                        moved = true;
+                    } else if (!same) {
                         h = hash_final(h, L, J.flags);
                         slot = insert_row_generic(J, s, L, h, nch, ncols, s_claims);
                         moved = slot != kFail;
@@ -895,6 +914,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         const uint64_t per = (cap + T - 1) / T;
         const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
         for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmpty;
+        if (J.algo == DFAMIN_ALG_LEADER)
+            for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) J.naive_new[i] = 0x7fffffff;
     }
     if (!team_barrier(ts)) goto done;
     trace_mark(J, tw, 0, 1);
@@ -952,7 +973,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         const int max_passes = J.max_passes;
         unsigned long long claims_seen = 0;
         int lead_reset_from = ld_volatile(&J.ctrl->nlead);   // initial leaders own no slot
-        while (count < n) {
+        const bool leader_mode = J.algo == DFAMIN_ALG_LEADER;
+        // signature rounds stop early once every block is a singleton; Alg. 2 runs until a
+        // round changes nothing
+        while (leader_mode || count < n) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
                 break;
@@ -963,8 +987,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             {
                 const int nlead = ld_volatile(&J.ctrl->nlead);
                 const int gid = rank * (int)blockDim.x + (int)threadIdx.x;
-                for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x)
-                    J.table[__ldcg(&J.lead_slot[i])] = kEmpty;
+                for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x) {
+                    if (leader_mode) J.naive_new[__ldcg(&J.lead_slot[i])] = 0x7fffffff;
+                    else J.table[__ldcg(&J.lead_slot[i])] = kEmpty;
+                }
                 lead_reset_from = nlead;
                 phase_leaders<KC>(J, rank, T, nlead, ncols);
             }
@@ -978,7 +1004,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             if constexpr (KC > 0) {
                 extern __shared__ __align__(16) unsigned char dsm[];
                 auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
-                use_cache = count <= kCacheMaxBlocks;
+                use_cache = !leader_mode && count <= kCacheMaxBlocks;
                 if (use_cache) {
                     cache_clear(cache);
                     __syncthreads();
@@ -990,7 +1016,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
             }
             __syncthreads();
-            if (threadIdx.x == 0 && s_claims) atomicAdd(&J.ctrl->claims, (unsigned long long)s_claims);
+            {
+                const int cl = leader_mode ? s_cnt : s_claims;   // leader mode: moved states
+                if (threadIdx.x == 0 && cl) atomicAdd(&J.ctrl->claims, (unsigned long long)cl);
+            }
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, passes, 5);
 
@@ -1037,7 +1066,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                 m = cache.gmin[ci];
                                 gs = cache.gslot[ci];
                             } else {
-                                m = (int)ld_relaxed_u32(&J.table[slot]);
+                                m = leader_mode ? ld_volatile(&J.naive_new[slot])
+                                                : (int)ld_relaxed_u32(&J.table[slot]);
                                 gs = slot;
                             }
                             J.block[s] = m;
@@ -1054,7 +1084,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                         if (i < cnt) {
                             s = J.lst_s[c0 + i];
                             gs = J.lst_slot[c0 + i];
-                            const int m = (int)ld_relaxed_u32(&J.table[gs]);
+                            const int m = leader_mode ? ld_volatile(&J.naive_new[gs])
+                                                      : (int)ld_relaxed_u32(&J.table[gs]);
                             J.block[s] = m;
                             lead = (m == s);
                         }
@@ -1074,7 +1105,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             }
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, passes, 6);
-            count += new_groups;
+            count = leader_mode ? ld_volatile(&J.ctrl->nlead) : count + new_groups;
         }
         if (ld_volatile(&J.ctrl->status) != 0) goto done;
 

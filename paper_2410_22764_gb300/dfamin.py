@@ -19,6 +19,7 @@ LIB_PATH = os.environ.get("DFAMIN_LIBRARY", os.path.join(_HERE, "libdfamin.so"))
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONVERGE, EPROBE = range(7)
 CLOSURE_OFF, CLOSURE_ON = 0, 1
+ALG_SIGNATURE, ALG_LEADER = 0, 1
 FLAG_KEEP_IDENTITY = 1
 FLAG_HASH_BLOCK_ONLY = 2
 FLAG_HASH_CONSTANT = 4
@@ -57,7 +58,7 @@ class Options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("ctas", ctypes.c_int32),
                 ("smem_states", ctypes.c_int32), ("team_states", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _load():
@@ -107,12 +108,13 @@ def status_string(code: int) -> str:
 
 
 def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: int = 0,
-            smem_states: int = 0, team_states: int = 0) -> Options:
+            smem_states: int = 0, team_states: int = 0, leader: bool = False) -> Options:
     o = Options()
     _lib.dfamin_default_options(ctypes.byref(o))
     o.closure = CLOSURE_ON if closure else CLOSURE_OFF
     o.max_passes, o.flags, o.ctas, o.smem_states = max_passes, flags, ctas, smem_states
     o.team_states = team_states
+    o.algorithm = ALG_LEADER if leader else ALG_SIGNATURE
     return o
 
 
@@ -229,11 +231,11 @@ def to_device(delta: np.ndarray, accept: np.ndarray, device="cuda"):
 
 def minimize_host(n: int, k: int, delta: np.ndarray, accept: np.ndarray, *,
                   closure: bool = False, flags: int = 0, max_passes: int = 0,
-                  device="cuda"):
+                  leader: bool = False, device="cuda"):
     """Convenience end-to-end call on host arrays; returns (block, nblocks, passes, status)."""
     d, a = to_device(delta, accept, device)
     r = minimize_ex(n, k, d, a, opt=options(closure=closure, flags=flags,
-                                            max_passes=max_passes))
+                                            max_passes=max_passes, leader=leader))
     return r.host()
 
 

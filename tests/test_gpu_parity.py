@@ -181,3 +181,52 @@ def test_workspace_reuse_and_streams(dm):
         got, gn, gp, st = r.host()
         want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
         assert st == 0 and gn == wn and np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- leader mode (Alg. 2 naivePR)
+def check_leader(dm, d, closure=False, **kw):
+    if closure:
+        dc, kc = oracle.closure_dfa(d.delta, d.n, d.k)
+        want, wn, wi = oracle.naive(dc, d.accept, d.n, kc)
+    else:
+        want, wn, wi = oracle.naive(d.delta, d.accept, d.n, d.k)
+    dlt, acc = dm.to_device(d.delta, d.accept)
+    r = dm.minimize_ex(d.n, d.k, dlt, acc, opt=dm.options(closure=closure, leader=True, **kw))
+    got, gn, gi, st = r.host()
+    assert st == 0 and gn == wn and gi == wi and np.array_equal(got, want)
+    return gi
+
+
+@pytest.mark.parametrize("maker", ["rand1", "rand2", "infl", "fib", "bits", "fig1", "path",
+                                   "tiny"])
+def test_leader_mode_against_naive_oracle(dm, maker):
+    d = {"rand1": lambda: I.random_dfa(3000, 3, 0.5, 1),
+         "rand2": lambda: I.random_dfa(50000, 12, 0.3, 2),
+         "infl": lambda: I.inflated_dfa(5000, 4, 4, 0.5, 3)[0],
+         "fib": lambda: I.cyclic_fib_dfa(14),
+         "bits": lambda: I.bitsplitter_dfa(12),
+         "fig1": I.fig1_dfa,
+         "path": lambda: I.path_fib_dfa(3000),
+         "tiny": lambda: I.random_dfa(2, 1, 0.5, 5)}[maker]()
+    check_leader(dm, d)
+    if maker in ("fib", "fig1", "path", "bits", "rand1"):
+        check_leader(dm, d, closure=True)             # transPR as Alg. transPR runs it
+
+
+def test_leader_mode_team_sizes(dm):
+    d = I.inflated_dfa(3000, 3, 4, 0.5, 11)[0]
+    for ctas in (1, 3, 32):
+        check_leader(dm, d, ctas=ctas)
+
+
+def test_leader_mode_batch(dm):
+    from test_gpu_batch import mixed_batch
+    dfas = mixed_batch(10, count=30, max_n=20000)
+    delta, acc, state_off, ks = dm.pack_batch(dfas)
+    plan = dm.BatchPlan(state_off, ks, dm.options(leader=True))
+    out, per = plan.run(torch.from_numpy(delta).cuda(), torch.from_numpy(acc.view(np.int32)).cuda())
+    torch.cuda.synchronize()
+    outs, p = plan.split(out.cpu().numpy()), per.cpu().numpy()
+    for i, d in enumerate(dfas):
+        want, wn, wi = oracle.naive(d.delta, d.accept, d.n, d.k)
+        assert p[2, i] == 0 and p[0, i] == wn and p[1, i] == wi and np.array_equal(outs[i], want)

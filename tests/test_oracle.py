@@ -330,3 +330,55 @@ def test_inflated_pass_count_from_base(seed):
     _, nb, ps = oracle.moore(d.delta, d.accept, d.n, d.k)
     _, bnb, bp = oracle.moore(base.delta, base.accept, base.n, base.k)
     assert nb == bnb and ps == bp + (1 if bnb == base.n else 0)
+
+
+# ---------------------------------------------------------------- Alg. 2 naivePR
+@pytest.mark.parametrize("seed", range(30))
+def test_naive_partition_equals_hopcroft(seed):
+    n, k = 1 + (seed * 53) % 400, seed % 5
+    d = I.random_dfa(n, k, [0.0, 0.3, 0.5, 1.0][seed % 4], seed)
+    b, nb, it = oracle.naive(d.delta, d.accept, n, k)
+    h, hn = oracle.hopcroft(d.delta, d.accept, n, k)
+    assert nb == hn and (b == h).all()
+    # every iteration but the last splits at least one block
+    assert 1 <= it <= max(1, nb - (1 if nb > 1 else 0)) + 1
+
+
+def test_naive_iterations_table2_fibonacci():
+    # Table 2, naivePR column: Fib with N states takes N-1 iterations (the last changes nothing)
+    for name, N, sig, size_out, iters in _read_golden("table2_rows.txt"):
+        if name.startswith("Fib"):
+            assert int(iters) == int(N) - 1
+    for i in range(3, 17):
+        d = I.cyclic_fib_dfa(i)
+        _, nb, it = oracle.naive(d.delta, d.accept, d.n, d.k)
+        assert nb == d.n and it == d.n - 1
+
+
+@pytest.mark.parametrize("nbits", range(1, 13))
+def test_naive_iterations_bitsplitter(nbits):
+    # Table 2 prints n-1 for B_n; counting, as Alg. 2 does, the final round that changes nothing
+    # gives n (the table's B rows omit that round, its Fib rows include it)
+    d = I.bitsplitter_dfa(nbits)
+    _, nb, it = oracle.naive(d.delta, d.accept, d.n, d.k)
+    assert nb == 1 << nbits and it == nbits
+
+
+def test_naive_fig1_and_closure():
+    d = I.fig1_dfa()
+    b, nb, it = oracle.naive(d.delta, d.accept, d.n, d.k)
+    assert nb == 10 and it == 9
+    dc, kc = oracle.closure_dfa(d.delta, d.n, d.k)
+    bc, nbc, itc = oracle.naive(dc, d.accept, d.n, kc)
+    assert nbc == 10 and (bc == b).all() and itc < it
+
+
+@pytest.mark.parametrize("i", [12, 16, 19])
+def test_naive_rounds_at_most_double_the_blocks(i):
+    # synchronous rounds split each block at most once, so r splitting rounds reach at most
+    # 2 * 2^r blocks; a round that read its own writes could beat this bound
+    d = I.cyclic_fib_dfa(i)
+    dc, kc = oracle.closure_dfa(d.delta, d.n, d.k)
+    for delta, k in ((d.delta, d.k), (dc, kc)):
+        _, nb, it = oracle.naive(delta, d.accept, d.n, k)
+        assert nb == d.n and 2 * 2 ** (it - 1) >= nb
