@@ -3,7 +3,7 @@
 n = 10,000,000, permuted ids, seed 1) on one GB300 per rank and print one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config2|random1k|path|batch4b|batch4a|serve]
+                  [--workload config2|random1k|path|batch4b|batch4a|serve|table2]
 
 A step is one full minimization (every refinement round until the partition is stable,
 plus the canonical renumbering) of the DFA already resident in HBM.  ``value`` is edge visits
@@ -191,9 +191,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve"])
+                    choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve",
+                             "table2"])
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--path-variant", default="both", choices=["both", "closure", "plain"])
+    ap.add_argument("--table2-rows", default="", help="comma-separated Table 2 rows (all)")
+    ap.add_argument("--table2-max-rounds", type=int, default=3_000_000,
+                    help="skip variants expected to take more refinement rounds than this")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -1,5 +1,5 @@
 """Measurement of the other workloads (one JSON line each), selected by
-``python bench.py --workload random1k|path|batch4b|batch4a|serve``.
+``python bench.py --workload random1k|path|batch4b|batch4a|serve|table2``.
 
 * random1k  random DFA n = 1,000, k = 2 (one CTA in shared memory): ms per minimization.
 * path      deep-refinement path n = 2^20, k = 2: plain rounds (534,348) against the closure.
@@ -8,6 +8,12 @@
 * batch4a   the same 4,096 draws uncapped (~6.5e9 transitions): one batched launch.
 * serve     Poisson request stream through the continuous-batching server at
             0.5 / 0.8 / 0.95 of its saturated throughput: p50 / p99 latency and DFAs/s.
+* table2    the paper's own families at the sizes of Table 2 (cyclic Fib with 17,711 ..
+            2,178,309 states, bit-splitters B_15 .. B_26 with up to 67M states and 25 letters),
+            each minimized by signature refinement (the sortPR rounds), the leader election
+            (naivePR), signature refinement on the closure (transPR as built here) and the leader
+            election on the closure (transPR as printed); the paper's times are carried as
+            context (other hardware).
 Timing: CUDA events on the launching stream, warm-up first, L2 flushed between timed steps
 (a 512 MB write) unless the inputs are larger than L2.
 """
@@ -228,6 +234,93 @@ def run_serve(args):
           sat["dfas_per_s"], "DFAs/s", 1e3 / sat["dfas_per_s"], R, 1, {"serve": runs})
 
 
+# Table 2 of the paper: name -> (N, |Sigma|, naivePR ms, sortPR ms, transPR ms); None = t/o or
+# OoM there.  Fib_i of the table has N = |w_{i+1}| states.
+TABLE2 = {
+    "Fib20": (17711, 1, 308.8, 3909.2, 1.7), "Fib21": (28657, 1, 494.2, 6374.2, 2.4),
+    "Fib22": (46368, 1, 778.7, 11712.1, 4.1), "Fib23": (75025, 1, 1241.3, 21366.6, 8.0),
+    "Fib24": (121393, 1, 2006.7, 34793.1, 12.5), "Fib25": (196418, 1, 3251.3, 64411.7, 18.3),
+    "Fib26": (317811, 1, 5277.8, 178367.4, 49.8), "Fib27": (514229, 1, 8607.7, None, 96.1),
+    "Fib28": (832040, 1, 22723.0, None, 178.4), "Fib29": (1346269, 1, 59510.8, None, 726.9),
+    "Fib30": (2178309, 1, 141601.0, None, 1109.3),
+    "B15": (32768, 14, 0.8, 25.8, 1.7), "B16": (65536, 15, 1.4, 29.7, 3.7),
+    "B17": (131072, 16, 2.6, 54.3, 9.4), "B18": (262144, 17, 5.0, 107.2, 25.6),
+    "B19": (524288, 18, 9.6, 235.7, 60.9), "B20": (1048576, 19, 19.3, 520.2, 139.8),
+    "B21": (2097152, 20, 39.8, 1148.6, 312.2), "B22": (4194304, 21, 82.6, 2538.5, 728.7),
+    "B23": (8388608, 22, 170.3, 5612.7, 1612.1), "B24": (16777216, 23, 352.6, 12351.8, None),
+    "B25": (33554432, 24, 737.4, 27092.2, None), "B26": (67108864, 25, 1541.5, 59203.8, None),
+}
+VARIANTS = (("sortPR", False, False), ("naivePR", False, True),
+            ("transPR", True, False), ("transPR_printed", True, True))
+
+
+def _table2_dfa(name):
+    if name.startswith("Fib"):
+        return I.cyclic_fib_dfa(int(name[3:]) + 1)
+    return I.bitsplitter_dfa(int(name[1:]))
+
+
+def _timed_runs(d, dd, aa, opt, reps, warmup):
+    """Median of `reps` timed minimizations (after `warmup` untimed ones) and the scalars."""
+    ws = dfamin.Workspace()
+    out = torch.empty(d.n, dtype=torch.int32, device="cuda")
+    sc = torch.zeros(3, dtype=torch.int32, device="cuda")
+    fn = lambda: dfamin.minimize_ex(d.n, d.k, dd, aa, opt=opt, workspace=ws,  # noqa: E731
+                                    out_block=out, scalars=sc)
+    ts = _time_steps(fn, reps, warmup)
+    nb, ps, st = sc.cpu().tolist()
+    del ws, out
+    torch.cuda.empty_cache()
+    return statistics.median(ts), nb, ps, st
+
+
+def run_table2(args):
+    rows, total = [], 0.0
+    for name, (N, k, p_naive, p_sort, p_trans) in TABLE2.items():
+        if args.table2_rows and name not in args.table2_rows.split(","):
+            continue
+        d = _table2_dfa(name)
+        assert d.n == N and d.k == k, (name, d.n, d.k)
+        dd, aa = dfamin.to_device(d.delta, d.accept)
+        row = {"name": name, "N": N, "k": k,
+               "paper_ms": {"naivePR": p_naive, "sortPR": p_sort, "transPR": p_trans}}
+        for vname, closure, leader in VARIANTS:
+            # deep plain refinement on Fib costs N rounds, and the leader election on the
+            # closure about N/2 rounds of N*(1 + log2 N) gathers: bounded by --table2-max-rounds
+            rounds = N if name.startswith("Fib") and not closure else 0
+            if name.startswith("Fib") and closure and leader:
+                rounds = N // 2 * (1 + int(np.log2(N)))
+            if rounds > args.table2_max_rounds:
+                row[vname] = {"skipped": f"about {rounds} rounds"}
+                continue
+            if closure:
+                need = dfamin.workspace_size(d.n, d.k, dfamin.options(closure=True))
+                free = torch.cuda.mem_get_info()[0]
+                if need > free - (2 << 30):
+                    row[vname] = {"enomem": f"workspace {need / 1e9:.0f} GB > free "
+                                            f"{free / 1e9:.0f} GB"}
+                    continue
+            opt = dfamin.options(closure=closure, leader=leader)
+            # runs of seconds are timed once, without a warm-up run of their own (the kernels
+            # were loaded by the rows before)
+            long = rounds > 100_000
+            reps = 1 if long else 3
+            ms, nb, ps, st = _timed_runs(d, dd, aa, opt, reps, 0 if long else 1)
+            assert st == 0 and nb == N, (name, vname, st, nb)
+            row[vname] = {"ms": ms, "iterations": ps, "steps": reps}
+            if vname == "transPR":
+                total += ms
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        del dd, aa
+        torch.cuda.empty_cache()
+    _line("paper families at Table 2 sizes: cyclic Fib (17,711..2,178,309 states, 1 letter) and "
+          "bit-splitters B_15..B_26 (2^15..2^26 states, 14..25 letters)", total, "ms",
+          total, 1, 1, {"rows": rows,
+                        "value_is": "sum over rows of the transPR (closure + signature) times"},
+          higher=False)
+
+
 def run(args):
     torch.cuda.set_device(0)
     if args.workload == "random1k":
@@ -238,4 +331,6 @@ def run(args):
         run_batch(args, args.workload[-2:])
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "table2":
+        run_table2(args)
     return 0

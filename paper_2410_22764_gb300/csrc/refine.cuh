@@ -857,6 +857,86 @@ static __device__ __forceinline__ void append_pair(const Job& J, int c0, int* cn
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Closure columns of Alg. transPR (Sec. 3.4), level-major: level i of every letter that is
+// still changing is stored in consecutive columns after those of level i-1.  Level i of letter a
+// is level i-1 applied twice.  When level i of a letter equals its level i-1 for every state,
+// every later level equals it too, so the letter gets no further levels; its level-i column (a
+// copy of level i-1) stays, since a repeated column changes no signature comparison.  With
+// DFAMIN_FLAG_KEEP_IDENTITY, or with more than kClSatLetters closed letters, every level of
+// every letter is built.  Letters are cl_letter[0..ncl); nonid[a] holds 1 (a is not the
+// identity) and then i+1 once level i of a is seen to differ from level i-1.
+// Team form (ts != nullptr): this CTA builds states [c0, c1) and every level ends with a team
+// barrier.  One-CTA form: states [0, n), __syncthreads.  Returns the number of closure columns,
+// or -1 when the team must stop.
+// ------------------------------------------------------------------------------------------
+constexpr int kClSatLetters = 128;
+
+static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamSync* ts, bool tw)
+{
+    __shared__ int s_act[kClSatLetters], s_src[kClSatLetters];
+    __shared__ int s_na;
+    const int n = J.n, k = J.k, lv = J.levels - 1;
+    const bool sat = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY) && ncl <= kClSatLetters;
+    if (sat) {
+        for (int r = threadIdx.x; r < ncl; r += blockDim.x) {
+            s_act[r] = __ldcg(&J.cl_letter[r]);
+            s_src[r] = -1;
+        }
+    }
+    __syncthreads();
+    int na = ncl, ncol = 0;
+    for (int i = 1; i <= lv && na > 0; ++i) {
+        for (int r = 0; r < na; ++r) {
+            const int a = sat ? s_act[r] : __ldcg(&J.cl_letter[r]);
+            const int src = sat ? s_src[r] : (i == 1 ? -1 : ncol - na + r);
+            const int32_t* prev = J.cl + (int64_t)src * n;
+            int32_t* cur = J.cl + (int64_t)(ncol + r) * n;
+            bool changed = false;
+            for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+                int t1, t;
+                if (src < 0) {
+                    t1 = __ldg(&J.delta[(int64_t)q * k + a]);
+                    t = __ldg(&J.delta[(int64_t)t1 * k + a]);
+                } else {
+                    t1 = __ldcg(&prev[q]);
+                    t = __ldcg(&prev[t1]);
+                }
+                cur[q] = t;
+                changed |= t != t1;
+            }
+            if (sat) {
+                if (__syncthreads_or(changed) && threadIdx.x == 0) J.nonid[a] = i + 1;
+            }
+        }
+        ncol += na;
+        if (ts) {
+            if (!team_barrier(*ts)) return -1;
+        } else {
+            __syncthreads();
+        }
+        trace_mark(J, tw, i, 3);
+        if (sat) {
+            if (threadIdx.x == 0) {
+                int m = 0;
+                for (int r = 0; r < na; ++r) {
+                    const int a = s_act[r];
+                    if (ld_volatile(&J.nonid[a]) == i + 1) {
+                        s_act[m] = a;
+                        s_src[m] = ncol - na + r;
+                        ++m;
+                    }
+                }
+                s_na = m;
+            }
+            __syncthreads();
+            na = s_na;
+            __syncthreads();
+        }
+    }
+    return ncol;
+}
+
 template <int KC>
 static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts)
 {
@@ -944,32 +1024,15 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
 
     {
         int count = (ld_volatile(&J.ctrl->min_f_rev) > 0) + (ld_volatile(&J.ctrl->min_n_rev) > 0);
-        const int ncl = closure ? ld_volatile(&J.ctrl->ncl_letters) : 0;
-        const int lv = J.levels - 1;
-
-        // ---- closure levels (Alg. transPR): level i of letter a is level i-1 applied twice
-        for (int i = 1; i <= lv && closure; ++i) {
-            for (int j = 0; j < ncl; ++j) {
-                const int a = __ldcg(&J.cl_letter[j]);
-                int32_t* cur = J.cl + ((int64_t)j * lv + (i - 1)) * n;
-                for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
-                    int t;
-                    if (i == 1) {
-                        t = __ldg(&J.delta[(int64_t)q * k + a]);
-                        t = __ldg(&J.delta[(int64_t)t * k + a]);
-                    } else {
-                        const int32_t* prev = cur - n;   // level i-1 of the same letter
-                        t = __ldcg(&prev[q]);
-                        t = __ldcg(&prev[t]);
-                    }
-                    cur[q] = t;
-                }
+        int ncl_cols = 0;
+        if constexpr (KC == 0) {
+            // ---- closure levels (Alg. transPR)
+            if (closure) {
+                ncl_cols = closure_build(J, c0, c1, ld_volatile(&J.ctrl->ncl_letters), &ts, tw);
+                if (ncl_cols < 0) goto done;
             }
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, i, 3);
         }
-
-        const int ncols = k + ncl * lv;
+        const int ncols = k + ncl_cols;
         const int max_passes = J.max_passes;
         unsigned long long claims_seen = 0;
         int lead_reset_from = ld_volatile(&J.ctrl->nlead);   // initial leaders own no slot
@@ -1236,8 +1299,7 @@ static __device__ void small_minimize(const Job& J, uint32_t cap)
     for (int s = threadIdx.x; s < n; s += blockDim.x)
         sblock[s] = is_accepting(J, s) ? mf : mn;
     count = (mf != 0x7fffffff) + (mn != 0x7fffffff);
-    int ncl = 0;
-    const int lv = J.levels - 1;
+    int ncl_cols = 0;
     if (closure) {
         __syncthreads();   // nonid[] complete
         if (threadIdx.x == 0) {
@@ -1247,28 +1309,9 @@ static __device__ void small_minimize(const Job& J, uint32_t cap)
             J.ctrl->ncl_letters = m;
         }
         __syncthreads();
-        ncl = J.ctrl->ncl_letters;
-        for (int i = 1; i <= lv; ++i) {
-            for (int j = 0; j < ncl; ++j) {
-                const int a = J.cl_letter[j];
-                int32_t* cur = J.cl + ((int64_t)j * lv + (i - 1)) * n;
-                for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    int t;
-                    if (i == 1) {
-                        t = __ldg(&J.delta[(int64_t)q * k + a]);
-                        t = __ldg(&J.delta[(int64_t)t * k + a]);
-                    } else {
-                        const int32_t* prev = cur - n;   // level i-1 of the same letter
-                        t = prev[q];
-                        t = prev[t];
-                    }
-                    cur[q] = t;
-                }
-            }
-            __syncthreads();
-        }
+        ncl_cols = closure_build(J, 0, n, J.ctrl->ncl_letters, nullptr, false);
     }
-    const int ncols = k + ncl * lv;
+    const int ncols = k + ncl_cols;
     __syncthreads();
 
     while (count < n) {

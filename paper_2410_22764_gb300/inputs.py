@@ -209,6 +209,8 @@ def bitsplitter_dfa(nbits: int) -> Dfa:
     """
     if nbits < 1:
         raise ValueError("nbits >= 1")
+    if nbits >= 16:
+        return bitsplitter_dfa_native(nbits)
     n = 1 << nbits
     k = nbits - 1
     x = np.arange(n, dtype=np.int64)
@@ -221,6 +223,21 @@ def bitsplitter_dfa(nbits: int) -> Dfa:
         delta[:, m - 1] = np.where(trigger, jumped, x)
     acc = ((x >> (nbits - 1)) & 1) == 1
     return Dfa(n, k, delta[:, :k].astype(np.int32).reshape(-1), pack_bits(acc))
+
+
+def bitsplitter_dfa_native(nbits: int, threads: int | None = None) -> Dfa:
+    """bitsplitter_dfa built by the multithreaded C generator (B_26 has 67M states)."""
+    import ctypes
+    import os
+    n, k = 1 << nbits, nbits - 1
+    delta = np.empty(n * k, dtype=np.int32)
+    accept = np.empty((n + 31) // 32, dtype=np.uint32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    rc = _native().inputs_bitsplitter(nbits, p(delta), p(accept),
+                                      threads or max(1, os.cpu_count() or 1))
+    if rc != 0:
+        raise RuntimeError(f"inputs_bitsplitter failed ({rc})")
+    return Dfa(n, k, delta, accept)
 
 
 def fig1_dfa() -> Dfa:
@@ -289,6 +306,9 @@ def _native():
         h = ctypes.CDLL(lib)
         h.inputs_random_batch.restype = ctypes.c_int
         h.inputs_random_batch.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 8 + [ctypes.c_int32]
+        h.inputs_bitsplitter.restype = ctypes.c_int
+        h.inputs_bitsplitter.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32]
         _NATIVE = h
     return _NATIVE
 

@@ -106,3 +106,63 @@ int inputs_random_batch(int32_t count, const int64_t *state_off, const int64_t *
     free(tid);
     return 0;
 }
+
+/*
+ * Bit-splitter B_nbits (same definition as inputs.bitsplitter_dfa): state x is a bit string,
+ * letter column m-1 (m = 1..nbits-1) maps x to (x with its low m+1 bits replaced by
+ * (not bit m) followed by m zeros) if bit m-1 of x is 1, and to x otherwise.  delta is
+ * state-major [2^nbits][nbits-1]; accept bit x is the top bit of x.
+ */
+typedef struct {
+    int32_t nbits;
+    int64_t x0, x1;
+    int32_t *delta;
+    uint32_t *accept;
+} bits_job_t;
+
+static void *bits_work(void *arg)
+{
+    const bits_job_t *J = (const bits_job_t *)arg;
+    const int32_t k = J->nbits - 1;
+    for (int64_t x = J->x0; x < J->x1; ++x) {
+        int32_t *row = J->delta + x * k;
+        for (int32_t m = 1; m <= k; ++m) {
+            const int64_t low = ((int64_t)1 << (m + 1)) - 1;
+            const int64_t b = (x >> m) & 1;
+            row[m - 1] = ((x >> (m - 1)) & 1) ? (int32_t)((x & ~low) | ((1 - b) << m))
+                                               : (int32_t)x;
+        }
+    }
+    /* accept words owned by this worker: x0 and x1 are multiples of 32 except at the end */
+    for (int64_t w = J->x0 / 32; w < (J->x1 + 31) / 32; ++w) {
+        uint32_t v = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int64_t x = w * 32 + j;
+            if (x < ((int64_t)1 << J->nbits) && ((x >> (J->nbits - 1)) & 1)) v |= 1u << j;
+        }
+        J->accept[w] = v;
+    }
+    return NULL;
+}
+
+int inputs_bitsplitter(int32_t nbits, int32_t *delta, uint32_t *accept, int32_t threads)
+{
+    if (nbits < 2 || nbits > 30 || threads < 1) return -1;
+    const int64_t n = (int64_t)1 << nbits;
+    bits_job_t *jobs = (bits_job_t *)calloc((size_t)threads, sizeof(bits_job_t));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tid) { free(jobs); free(tid); return -2; }
+    for (int t = 0; t < threads; ++t) {
+        bits_job_t *J = &jobs[t];
+        J->nbits = nbits;
+        J->x0 = (n / 32) * t / threads * 32;
+        J->x1 = t + 1 == threads ? n : (n / 32) * (t + 1) / threads * 32;
+        J->delta = delta;
+        J->accept = accept;
+        pthread_create(&tid[t], NULL, bits_work, J);
+    }
+    for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+    free(jobs);
+    free(tid);
+    return 0;
+}

@@ -230,3 +230,45 @@ def test_leader_mode_batch(dm):
     for i, d in enumerate(dfas):
         want, wn, wi = oracle.naive(d.delta, d.accept, d.n, d.k)
         assert p[2, i] == 0 and p[0, i] == wn and p[1, i] == wi and np.array_equal(outs[i], want)
+
+
+# ---------------------------------------------------------------- closure saturation
+def closure_levels_built(dm, d, flags=0, leader=False):
+    ws = dm.Workspace()
+    opt = dm.options(closure=True, flags=flags | dm.FLAG_TRACE, smem_states=1, leader=leader)
+    dlt, acc = dm.to_device(d.delta, d.accept)
+    r = dm.minimize_ex(d.n, d.k, dlt, acc, opt=opt, workspace=ws)
+    got, gn, gp, st = r.host()
+    assert st == 0
+    return sum(1 for _, ph, _ in dm.read_trace(ws, d.n, d.k, opt) if ph == "closure"), gp
+
+
+@pytest.mark.parametrize("nbits", [6, 10, 13])
+def test_closure_stops_at_fixed_point_letters(dm, nbits):
+    # every bit-splitter letter is idempotent (a^2 = a): one closure level is built, not
+    # floor(log2 n); partition and passes still equal Moore on the full A'
+    d = I.bitsplitter_dfa(nbits)
+    check(dm, d, closure=True)
+    lv, gp = closure_levels_built(dm, d)
+    assert lv == 1
+    lv_all, gp_all = closure_levels_built(dm, d, flags=dm.FLAG_KEEP_IDENTITY)
+    assert lv_all == nbits and gp_all == gp
+
+
+def test_closure_saturation_mixed_letters(dm):
+    # letter 0 cycles (never saturates), letter 1 collapses onto a fixed point after a few
+    # steps, letter 2 is the identity: results must match the oracle's full closure
+    rng = np.random.default_rng(3)
+    n = 5000
+    delta = np.empty((n, 3), np.int32)
+    delta[:, 0] = (np.arange(n) + 1) % n
+    delta[:, 1] = np.maximum(np.arange(n) - 7, 0) // 2
+    delta[:, 2] = np.arange(n)
+    acc = I.pack_bits(rng.random(n) < 0.5)
+    d = I.Dfa(n, 3, delta.reshape(-1), acc)
+    check(dm, d, closure=True)
+    check(dm, d, closure=True, smem_states=1)
+    check(dm, d, closure=True, flags=dm.FLAG_KEEP_IDENTITY, smem_states=1)
+    check_leader(dm, d, closure=True)
+    lv, _ = closure_levels_built(dm, d)
+    assert lv == int(np.log2(n))          # letter 0 needs every level

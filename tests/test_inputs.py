@@ -1,5 +1,6 @@
 """Checks of the seeded input generators against their published definitions."""
 import numpy as np
+import pytest
 
 from paper_2410_22764_gb300 import inputs as I
 
@@ -79,3 +80,12 @@ def test_native_batch_generator_matches_numpy():
         assert got.n == want.n and got.k == want.k
         assert np.array_equal(got.delta, want.delta)
         assert np.array_equal(got.accepting(), want.accepting())
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_native_bitsplitter_matches_numpy(threads):
+    for nbits in range(2, 15):
+        a = I.bitsplitter_dfa(nbits)
+        b = I.bitsplitter_dfa_native(nbits, threads=threads)
+        assert (a.n, a.k) == (b.n, b.k)
+        assert np.array_equal(a.delta, b.delta) and np.array_equal(a.accept, b.accept)
