@@ -63,6 +63,10 @@ def _load():
             lib.oracle_check_stable.argtypes = [i32, i32, p, p, p]
             lib.oracle_naive.argtypes = [i32, i32, p, p, i32, p, p, p]
             lib.oracle_naive.restype = ctypes.c_int
+            lib.oracle_reachable.argtypes = [i32, i32, p, i32, p, p]
+            lib.oracle_reachable.restype = ctypes.c_int
+            lib.oracle_quotient.argtypes = [i32, i32, p, p, p, i32, i32, p, p, p]
+            lib.oracle_quotient.restype = ctypes.c_int
             for f in (lib.oracle_canonical, lib.oracle_moore, lib.oracle_hopcroft,
                       lib.oracle_tablefill, lib.oracle_closure, lib.oracle_check_stable):
                 f.restype = ctypes.c_int
@@ -183,3 +187,54 @@ def check_stable(delta, accept, n: int, k: int, labels) -> bool:
     if rc < 0:
         raise ValueError(f"oracle_check_stable failed ({rc})")
     return rc == 1
+
+
+def reachable(delta, n: int, k: int, q0: int):
+    """States reachable from q0 (Sec. 2): (newid, count), newid[s] = rank of s among the
+    reachable states in increasing order, -1 if unreachable."""
+    delta = np.ascontiguousarray(delta, dtype=np.int32)
+    out = np.empty(n, np.int32)
+    cnt = ctypes.c_int32(0)
+    rc = _load().oracle_reachable(n, k, _ptr(delta), q0, _ptr(out), ctypes.byref(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle_reachable failed ({rc})")
+    return out, cnt.value
+
+
+def induced(delta, accept, n: int, k: int, newid, count: int):
+    """The sub-DFA on the reachable states, renumbered by newid (a plain restriction: every
+    successor of a reachable state is reachable)."""
+    delta = np.asarray(delta, dtype=np.int32).reshape(n, k) if k else np.zeros((n, 0), np.int32)
+    keep = np.flatnonzero(newid >= 0)
+    assert keep.size == count
+    rdelta = newid[delta[keep]].astype(np.int32).reshape(-1)
+    bits = (np.asarray(accept, dtype=np.uint32)[keep >> 5] >> (keep & 31).astype(np.uint32)) & 1
+    racc = np.zeros((count + 31) // 32, np.uint32)
+    np.bitwise_or.at(racc, np.arange(count) >> 5, (bits << (np.arange(count) & 31)).astype(np.uint32))
+    return rdelta, racc
+
+
+def quotient(delta, accept, n: int, k: int, block, nblocks: int, q0: int):
+    """Quotient automaton of a stable partition (Sec. 2): (delta' [nblocks*k], accept' bitmap,
+    q0')."""
+    delta, accept = _prep(delta, accept, n, k)
+    block = np.ascontiguousarray(block, dtype=np.int32)
+    qd = np.empty(max(nblocks * k, 1), np.int32)
+    qa = np.empty((nblocks + 31) // 32, np.uint32)
+    q0o = ctypes.c_int32(0)
+    rc = _load().oracle_quotient(n, k, _ptr(delta), _ptr(accept), _ptr(block), nblocks, q0,
+                                 _ptr(qd), _ptr(qa), ctypes.byref(q0o))
+    if rc != 0:
+        raise ValueError(f"oracle_quotient failed ({rc})")
+    return qd[: nblocks * k], qa, q0o.value
+
+
+def minimal_dfa(delta, accept, n: int, k: int, q0: int):
+    """The minimal DFA of (delta, accept, q0) (Sec. 2): unreachable states removed, then
+    equivalent states merged (Hopcroft, canonical ids).  Returns (delta', accept', nstates,
+    q0', nreach)."""
+    newid, cnt = reachable(delta, n, k, q0)
+    rdelta, racc = induced(delta, accept, n, k, newid, cnt)
+    block, nb = hopcroft(rdelta, racc, cnt, k)
+    qd, qa, q0m = quotient(rdelta, racc, cnt, k, block, nb, int(newid[q0]))
+    return qd, qa, nb, q0m, cnt

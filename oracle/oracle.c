@@ -24,6 +24,8 @@
  *   oracle_tablefill   pairwise marking: the sequential meaning of Alg. 1 "trans" (Sec. 3.1)
  *   oracle_closure     the per-letter partial transitive closure of Alg. transPR (Sec. 3.4)
  *   oracle_naive       leader-election refinement, the steps of Alg. 2 naivePR (Sec. 3.2)
+ *   oracle_reachable   states reachable from q0, order-preserving renumbering (Sec. 2)
+ *   oracle_quotient    the quotient automaton of a stable partition (Sec. 2)
  *   oracle_check_stable  property check: refines {F, Q\F} and is stable under delta
  *
  * Every routine returns 0 on success and a negative value on bad arguments or allocation
@@ -585,4 +587,71 @@ int oracle_naive(int32_t n, int32_t k, const int32_t *delta, const uint32_t *acc
         *iters = it;
     free(block); free(next); free(new_leader); free(differs);
     return rc;
+}
+
+/*
+ * Reachable states (Sec. 2: minimization deletes the states that no word leads to from q0).
+ * Plain breadth-first search from q0 with a FIFO queue.  out_newid[s] is the rank of s among
+ * the reachable states in increasing state order (an order-preserving renumbering), or -1;
+ * *count is the number of reachable states.
+ */
+int oracle_reachable(int32_t n, int32_t k, const int32_t *delta, int32_t q0, int32_t *out_newid,
+                     int32_t *count)
+{
+    if (n < 1 || k < 0 || q0 < 0 || q0 >= n || !out_newid || !count || (k > 0 && !delta))
+        return ORACLE_EARG;
+    if (check_delta(n, k, delta)) return ORACLE_EARG;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    char *seen = (char *)calloc((size_t)n, 1);
+    if (!queue || !seen) { free(queue); free(seen); return ORACLE_ENOMEM; }
+    int32_t head = 0, tail = 0;
+    queue[tail++] = q0;
+    seen[q0] = 1;
+    while (head < tail) {
+        const int32_t s = queue[head++];
+        for (int32_t a = 0; a < k; ++a) {
+            const int32_t t = delta[(int64_t)s * k + a];
+            if (!seen[t]) { seen[t] = 1; queue[tail++] = t; }
+        }
+    }
+    int32_t c = 0;
+    for (int32_t s = 0; s < n; ++s) out_newid[s] = seen[s] ? c++ : -1;
+    *count = c;
+    free(queue);
+    free(seen);
+    return ORACLE_OK;
+}
+
+/*
+ * Quotient automaton A/~ (Sec. 2, "combining undistinguishable states"): given a partition
+ * `block` of the states into nblocks classes, each stable under delta and refining {F, Q\F},
+ * the class B goes to class block[delta(s, a)] on letter a for any s in B (stability makes the
+ * choice irrelevant; the smallest state of B is used), B accepts iff its states do, and the
+ * initial class is block[q0].  out_delta is [nblocks][k] state-major; out_accept a bitmap.
+ */
+int oracle_quotient(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,
+                    const int32_t *block, int32_t nblocks, int32_t q0, int32_t *out_delta,
+                    uint32_t *out_accept, int32_t *out_q0)
+{
+    if (n < 1 || k < 0 || nblocks < 1 || nblocks > n || q0 < 0 || q0 >= n || !accept ||
+        !block || !out_accept || !out_q0 || (k > 0 && (!delta || !out_delta)))
+        return ORACLE_EARG;
+    int32_t *rep = (int32_t *)malloc(sizeof(int32_t) * (size_t)nblocks);
+    if (!rep) return ORACLE_ENOMEM;
+    for (int32_t b = 0; b < nblocks; ++b) rep[b] = -1;
+    for (int32_t s = n - 1; s >= 0; --s) {
+        if (block[s] < 0 || block[s] >= nblocks) { free(rep); return ORACLE_EARG; }
+        rep[block[s]] = s;
+    }
+    for (int32_t b = 0; b < nblocks; ++b)
+        if (rep[b] < 0) { free(rep); return ORACLE_EARG; }
+    memset(out_accept, 0, sizeof(uint32_t) * (size_t)((nblocks + 31) / 32));
+    for (int32_t b = 0; b < nblocks; ++b) {
+        for (int32_t a = 0; a < k; ++a)
+            out_delta[(int64_t)b * k + a] = block[delta[(int64_t)rep[b] * k + a]];
+        if (is_accepting(accept, rep[b])) out_accept[b >> 5] |= 1u << (b & 31);
+    }
+    *out_q0 = block[q0];
+    free(rep);
+    return ORACLE_OK;
 }

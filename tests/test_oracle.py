@@ -382,3 +382,97 @@ def test_naive_rounds_at_most_double_the_blocks(i):
     for delta, k in ((d.delta, d.k), (dc, kc)):
         _, nb, it = oracle.naive(delta, d.accept, d.n, k)
         assert nb == d.n and 2 * 2 ** (it - 1) >= nb
+
+
+# ---------------------------------------------------------------- reachability and quotient
+def _run_word(delta, k, accept, q, word):
+    for a in word:
+        q = int(delta[q * k + a])
+    return bool((int(accept[q >> 5]) >> (q & 31)) & 1)
+
+
+def _bfs_canonical(delta, accept, n, k, q0):
+    """Relabel a fully reachable DFA by first visit in a BFS from q0 taking letters in order:
+    two isomorphic DFAs get the same (delta, accept-list)."""
+    order, pos = [q0], {q0: 0}
+    i = 0
+    while i < len(order):
+        s = order[i]
+        i += 1
+        for a in range(k):
+            t = int(delta[s * k + a])
+            if t not in pos:
+                pos[t] = len(order)
+                order.append(t)
+    assert len(order) == n
+    d = [pos[int(delta[s * k + a])] for s in order for a in range(k)]
+    acc = [int((int(accept[s >> 5]) >> (s & 31)) & 1) for s in order]
+    return d, acc
+
+
+def test_reachable_hand_example():
+    # 0 -> 1 -> 0, 2 loops, 3 -> 0; only 1 accepts; from 0: {0, 1}; 2 and 3 unreachable
+    delta = np.array([1, 0, 2, 0], np.int32)
+    acc = I.pack_bits(np.array([0, 1, 0, 0], bool))
+    newid, cnt = oracle.reachable(delta, 4, 1, 0)
+    assert cnt == 2 and newid.tolist() == [0, 1, -1, -1]
+    qd, qa, nb, q0, nr = oracle.minimal_dfa(delta, acc, 4, 1, 0)
+    assert (nb, q0, nr) == (2, 0, 2) and qd.tolist() == [1, 0] and int(qa[0]) == 0b10
+    # from 3: 3 -> 0 -> 1 -> 0 ...; a from 3 rejects but a from 0 accepts, so 3, 0 and 1 are
+    # pairwise distinguishable: three states, renumbered 0 (was 0), 1 (was 1), 2 (was 3)
+    qd, qa, nb, q0, nr = oracle.minimal_dfa(delta, acc, 4, 1, 3)
+    assert (nb, nr, q0) == (3, 3, 2) and qd.tolist() == [1, 0, 0] and int(qa[0]) == 0b010
+
+
+def test_reachable_union_and_degenerate_cases():
+    # a single cycle (Fib) next to a random DFA: from a cycle state exactly the cycle is reached
+    a = I.cyclic_fib_dfa(10)
+    b = I.random_dfa(500, 1, 0.5, 3)
+    n = a.n + b.n
+    delta = np.concatenate([a.delta, b.delta + a.n]).astype(np.int32)
+    newid, cnt = oracle.reachable(delta, n, 1, 17)
+    assert cnt == a.n and (newid[:a.n] == np.arange(a.n)).all() and (newid[a.n:] == -1).all()
+    # bit-splitter from state 0: no letter fires, one reachable state, a one-state minimal DFA
+    d = I.bitsplitter_dfa(8)
+    qd, qa, nb, q0, nr = oracle.minimal_dfa(d.delta, d.accept, d.n, d.k, 0)
+    assert (nb, nr, q0) == (1, 1, 0) and (qd == 0).all() and int(qa[0]) == 0
+    # k = 0: only q0 is reachable
+    newid, cnt = oracle.reachable(np.zeros(0, np.int32), 5, 0, 2)
+    assert cnt == 1 and newid.tolist() == [-1, -1, 0, -1, -1]
+    # Fig. 1 from q0 = 0: all 10 states, already minimal
+    d = I.fig1_dfa()
+    qd, qa, nb, q0, nr = oracle.minimal_dfa(d.delta, d.accept, d.n, d.k, 0)
+    assert (nb, nr, q0) == (10, 10, 0) and qd.tolist() == d.delta.tolist()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_minimal_dfa_language_and_minimality(seed):
+    rng = np.random.default_rng(seed)
+    n, k = int(rng.integers(2, 300)), int(rng.integers(1, 4))
+    if seed % 3 == 0:
+        d = I.inflated_dfa(max(1, n // 4), k, 4, 0.5, seed)[0]
+    else:
+        d = I.random_dfa(n, k, 0.5, seed)
+    # make part of the automaton unreachable: a second copy whose states nothing enters
+    n2 = 2 * d.n
+    delta = np.concatenate([d.delta, d.delta + d.n]).astype(np.int32)
+    acc = I.pack_bits(np.concatenate([I.unpack_bits(d.accept, d.n)] * 2))
+    q0 = int(rng.integers(0, d.n))
+    qd, qa, nb, q0m, nr = oracle.minimal_dfa(delta, acc, n2, d.k, q0)
+    assert nr <= d.n
+    # same language: random words from q0 and q0'
+    for _ in range(300):
+        w = rng.integers(0, d.k, size=int(rng.integers(0, 3 * d.n)))
+        assert _run_word(delta, d.k, acc, q0, w) == _run_word(qd, d.k, qa, q0m, w)
+    # minimal: every state reachable and no two states equivalent
+    assert oracle.reachable(qd, nb, d.k, q0m)[1] == nb
+    assert oracle.hopcroft(qd, qa, nb, d.k)[1] == nb
+    # unique up to isomorphism (Myhill-Nerode): a permuted copy gives the same canonical form
+    perm = rng.permutation(n2).astype(np.int32)
+    pd = np.empty_like(delta).reshape(n2, d.k)
+    pd[perm] = perm[delta.reshape(n2, d.k)]
+    pacc = I.pack_bits(np.array([I.unpack_bits(acc, n2)[np.argsort(perm)][i]
+                                 for i in range(n2)], bool))
+    qd2, qa2, nb2, q0m2, nr2 = oracle.minimal_dfa(pd.reshape(-1), pacc, n2, d.k, int(perm[q0]))
+    assert (nb2, nr2) == (nb, nr)
+    assert _bfs_canonical(qd, qa, nb, d.k, q0m) == _bfs_canonical(qd2, qa2, nb2, d.k, q0m2)
