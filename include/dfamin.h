@@ -68,9 +68,11 @@ typedef enum {
                                   this is transPR exactly as Alg. transPR runs it (naivePR on A') */
 
 /* flags */
-#define DFAMIN_FLAG_KEEP_IDENTITY 1u  /* closure: also close letters whose delta is the identity
-                                         (by default their columns, all equal to the identity,
-                                         are left out; this changes no partition and no pass) */
+#define DFAMIN_FLAG_KEEP_IDENTITY 1u  /* closure: build every column of A'.  By default letters
+                                         whose delta is the identity get no closure columns, and
+                                         a letter stops getting levels once level i equals level
+                                         i-1 (every later level would repeat it); repeated
+                                         columns change no partition and no pass count */
 #define DFAMIN_FLAG_HASH_BLOCK_ONLY 2u /* testing: hash only the old block id (forces collisions
                                          that the full-tuple check must resolve) */
 #define DFAMIN_FLAG_HASH_CONSTANT 4u   /* testing: constant hash (every group collides) */
@@ -201,6 +203,76 @@ dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int32_t *delta,
                                      const uint32_t *accept, int32_t *out_block,
                                      int32_t *nblocks, const dfamin_options *opt,
                                      int32_t *passes, int32_t *status, dfamin_stream_t stream);
+
+
+/*
+ * Reachability and the minimal DFA (Sec. 2: minimizing a DFA merges indistinguishable states and
+ * deletes the states unreachable from the initial state q0; the paper's refinement algorithms
+ * assume the deletion was done as a pre-processing step).  The paper prints no algorithm for
+ * these steps; they are plain definitions.
+ *
+ * dfamin_reachable - states reachable from q0 by some word.
+ *   out_newid  int32 [n]: the rank of s among the reachable states in increasing state order
+ *              (an order-preserving renumbering), or -1 if s is unreachable.
+ *   out_delta  int32 [n*k] or NULL: the sub-DFA induced by the reachable states, renumbered:
+ *              out_delta[newid[s]*k + a] = newid[delta(s, a)]; the first count*k entries are
+ *              written.
+ *   out_accept uint32 bitmap [(n+31)/32] or NULL: bit newid[s] is set iff s accepts (the
+ *              whole bitmap is cleared first).
+ *   count      device int32 or NULL: number of reachable states (or -status on a device error).
+ *   status     device int32 or NULL: DFAMIN_OK, or DFAMIN_EINVAL if a row of a reachable state
+ *              holds an entry outside [0, n) (rows of unreachable states are not read), or
+ *              DFAMIN_ETIMEOUT.
+ *   workspace  device, 256-byte aligned, dfamin_reach_workspace_size(n) bytes.
+ * Breadth-first search; a chain of L states takes about L/256 barrier-separated levels and L
+ * dependent loads, so long chains are latency-bound.
+ */
+dfamin_status dfamin_reach_workspace_size(int32_t n, size_t *bytes);
+dfamin_status dfamin_reachable(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,
+                               int32_t q0, int32_t *out_newid, int32_t *out_delta,
+                               uint32_t *out_accept, int32_t *count, int32_t *status,
+                               void *workspace, size_t workspace_bytes, dfamin_stream_t stream);
+
+/*
+ * dfamin_quotient - the quotient automaton of a partition (Sec. 2, combining states).
+ *   block      int32 [n]: class of every state, any ids in [0, n) (for example out_block of
+ *              dfamin_minimize_ex).  The partition must be stable under delta for the result to
+ *              be the quotient; the class of delta(rep, a) is taken from the class's smallest
+ *              member rep.
+ *   newid      int32 [n] or NULL: out_newid of dfamin_reachable on the same DFA; only states
+ *              with newid[s] >= 0 are kept (q0 must be one of them).  NULL keeps every state.
+ *   out_delta  int32 [n*k] capacity: out_delta[B*k + a] for the nstates output classes, which
+ *              are numbered in the order of their smallest kept member.
+ *   out_accept uint32 bitmap [(n+31)/32] (cleared first): bit B set iff class B accepts.
+ *   nstates    device int32: number of classes (or -status); out_q0 device int32 or NULL: the
+ *              class of q0; status device int32 or NULL.
+ *   workspace  device, 256-byte aligned, dfamin_quotient_workspace_size(n) bytes.
+ */
+dfamin_status dfamin_quotient_workspace_size(int32_t n, size_t *bytes);
+dfamin_status dfamin_quotient(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,
+                              const int32_t *block, int32_t q0, const int32_t *newid,
+                              int32_t *out_delta, uint32_t *out_accept, int32_t *nstates,
+                              int32_t *out_q0, int32_t *status, void *workspace,
+                              size_t workspace_bytes, dfamin_stream_t stream);
+
+/*
+ * dfamin_minimal_dfa - the minimal DFA of (delta, accept, q0): dfamin_reachable, the
+ * refinement of dfamin_minimize_ex (with `opt`) on the whole DFA, and dfamin_quotient restricted
+ * to the reachable states, enqueued on `stream` with no host synchronisation.  Classes of the
+ * whole DFA restricted to the reachable states are the classes of the reachable sub-DFA
+ * (equivalence of two states depends only on the states reachable from them).
+ *   out_delta   int32 [n*k] capacity, out_accept uint32 [(n+31)/32]: the minimal DFA, states
+ *               numbered in the order of their smallest reachable member.
+ *   out_scalars device int32 [5]: nstates (or -status), q0 of the minimal DFA, number of
+ *               reachable states, refinement passes, status (first error of any stage).
+ *   workspace   device, 256-byte aligned, dfamin_minimal_dfa_workspace_size(n, k, opt) bytes.
+ */
+dfamin_status dfamin_minimal_dfa_workspace_size(int32_t n, int32_t k, const dfamin_options *opt,
+                                                size_t *bytes);
+dfamin_status dfamin_minimal_dfa(int32_t n, int32_t k, const int32_t *delta,
+                                 const uint32_t *accept, int32_t q0, const dfamin_options *opt,
+                                 int32_t *out_delta, uint32_t *out_accept, int32_t *out_scalars,
+                                 void *workspace, size_t workspace_bytes, dfamin_stream_t stream);
 
 /* Text of the last CUDA runtime failure seen by the library on the calling thread ("" if
  * none); meant for diagnostics after DFAMIN_ECUDA / DFAMIN_ENOMEM.  Thread-local storage. */

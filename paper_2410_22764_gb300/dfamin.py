@@ -42,6 +42,12 @@ ABI_FUNCTIONS = (
     "dfamin_batch_workspace_size",
     "dfamin_batch_plan_info",
     "dfamin_minimize_batch",
+    "dfamin_reach_workspace_size",
+    "dfamin_reachable",
+    "dfamin_quotient_workspace_size",
+    "dfamin_quotient",
+    "dfamin_minimal_dfa_workspace_size",
+    "dfamin_minimal_dfa",
 )
 
 
@@ -87,6 +93,18 @@ def _load():
     for f in (lib.dfamin_batch_plan_create, lib.dfamin_batch_plan_destroy,
               lib.dfamin_batch_workspace_size, lib.dfamin_batch_plan_info,
               lib.dfamin_minimize_batch):
+        f.restype = ctypes.c_int
+    lib.dfamin_reach_workspace_size.argtypes = [i32, ctypes.POINTER(sz)]
+    lib.dfamin_reachable.argtypes = [i32, i32, p, p, i32, p, p, p, p, p, p, sz, p]
+    lib.dfamin_quotient_workspace_size.argtypes = [i32, ctypes.POINTER(sz)]
+    lib.dfamin_quotient.argtypes = [i32, i32, p, p, p, i32, p, p, p, p, p, p, p, sz, p]
+    lib.dfamin_minimal_dfa_workspace_size.argtypes = [i32, i32, ctypes.POINTER(Options),
+                                                      ctypes.POINTER(sz)]
+    lib.dfamin_minimal_dfa.argtypes = [i32, i32, p, p, i32, ctypes.POINTER(Options), p, p, p, p,
+                                       sz, p]
+    for f in (lib.dfamin_reach_workspace_size, lib.dfamin_reachable,
+              lib.dfamin_quotient_workspace_size, lib.dfamin_quotient,
+              lib.dfamin_minimal_dfa_workspace_size, lib.dfamin_minimal_dfa):
         f.restype = ctypes.c_int
     lib.dfamin_last_cuda_error.argtypes = []
     lib.dfamin_last_cuda_error.restype = ctypes.c_char_p
@@ -220,6 +238,86 @@ def minimize(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
     if rc:
         raise DfaminError(rc, "dfamin_minimize")
     return out_block, nblocks
+
+
+def _check_dfa(n, k, delta, accept):
+    dev = delta.device if k > 0 else accept.device
+    if dev.type != "cuda" or accept.device.type != "cuda":
+        raise ValueError("delta and accept must be CUDA tensors")
+    if k > 0 and (delta.dtype != torch.int32 or delta.numel() != n * k
+                  or not delta.is_contiguous()):
+        raise ValueError("delta must be a contiguous int32 tensor of n*k entries")
+    if accept.element_size() != 4 or accept.numel() < (n + 31) // 32:
+        raise ValueError("accept must be a 32-bit bitmap of (n+31)//32 words")
+    return dev
+
+
+def _size(fn, *args) -> int:
+    out = ctypes.c_size_t(0)
+    rc = fn(*args, ctypes.byref(out))
+    if rc:
+        raise DfaminError(rc, fn.__name__)
+    return out.value
+
+
+def reachable(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, q0: int, *,
+              induced: bool = True, workspace: Workspace | None = None, stream=None):
+    """Enqueue dfamin_reachable.  Returns device tensors (newid [n], delta' [n*k] or None,
+    accept' [(n+31)//32] or None, scalars [2] = count, status)."""
+    dev = _check_dfa(n, k, delta, accept)
+    ws = (workspace or Workspace(dev)).get(_size(_lib.dfamin_reach_workspace_size, n))
+    newid = torch.empty(n, dtype=torch.int32, device=dev)
+    rd = torch.empty(max(n * k, 1), dtype=torch.int32, device=dev) if induced else None
+    ra = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev) if induced else None
+    sc = torch.zeros(2, dtype=torch.int32, device=dev)
+    rc = _lib.dfamin_reachable(n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0), _ptr(accept),
+                               q0, _ptr(newid), _ptr(rd), _ptr(ra), ctypes.c_void_p(sc.data_ptr()),
+                               ctypes.c_void_p(sc.data_ptr() + 4), _ptr(ws),
+                               ctypes.c_size_t(ws.numel()), _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_reachable")
+    return newid, rd, ra, sc
+
+
+def quotient(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, block: torch.Tensor,
+             q0: int, newid: torch.Tensor | None = None, *, workspace: Workspace | None = None,
+             stream=None):
+    """Enqueue dfamin_quotient.  Returns device tensors (delta' [n*k] capacity, accept' bitmap,
+    scalars [3] = nstates, q0', status)."""
+    dev = _check_dfa(n, k, delta, accept)
+    ws = (workspace or Workspace(dev)).get(_size(_lib.dfamin_quotient_workspace_size, n))
+    qd = torch.empty(max(n * k, 1), dtype=torch.int32, device=dev)
+    qa = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    sc = torch.zeros(3, dtype=torch.int32, device=dev)
+    sp = sc.data_ptr()
+    rc = _lib.dfamin_quotient(n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0), _ptr(accept),
+                              _ptr(block), q0, _ptr(newid), _ptr(qd), _ptr(qa),
+                              ctypes.c_void_p(sp), ctypes.c_void_p(sp + 4),
+                              ctypes.c_void_p(sp + 8), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                              _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_quotient")
+    return qd, qa, sc
+
+
+def minimal_dfa(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, q0: int, *,
+                opt: Options | None = None, workspace: Workspace | None = None, stream=None):
+    """Enqueue dfamin_minimal_dfa.  Returns device tensors (delta' [n*k] capacity, accept'
+    bitmap, scalars [5] = nstates, q0', reachable states, passes, status)."""
+    opt = opt or options()
+    dev = _check_dfa(n, k, delta, accept)
+    ws = (workspace or Workspace(dev)).get(
+        _size(_lib.dfamin_minimal_dfa_workspace_size, n, k, ctypes.byref(opt)))
+    qd = torch.empty(max(n * k, 1), dtype=torch.int32, device=dev)
+    qa = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    sc = torch.zeros(5, dtype=torch.int32, device=dev)
+    rc = _lib.dfamin_minimal_dfa(n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0),
+                                 _ptr(accept), q0, ctypes.byref(opt), _ptr(qd), _ptr(qa),
+                                 ctypes.c_void_p(sc.data_ptr()), _ptr(ws),
+                                 ctypes.c_size_t(ws.numel()), _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimal_dfa")
+    return qd, qa, sc
 
 
 def to_device(delta: np.ndarray, accept: np.ndarray, device="cuda"):
