@@ -274,6 +274,27 @@ dfamin_status dfamin_minimal_dfa(int32_t n, int32_t k, const int32_t *delta,
                                  int32_t *out_delta, uint32_t *out_accept, int32_t *out_scalars,
                                  void *workspace, size_t workspace_bytes, dfamin_stream_t stream);
 
+/*
+ * dfamin_lts_determinize - LTS -> DFA front end (Sec. 4.1, "VLTSs"): the powerset construction
+ * from s0 makes the LTS deterministic; every subset state accepts; one extra non-accepting state
+ * (bottom) receives every missing transition and loops on every label.  HOST code on HOST
+ * arrays (it prepares input for the device calls; it runs on the calling thread and uses no
+ * GPU).
+ *   n, nlabels, m   states, labels and transitions of the LTS; transition i is
+ *                   src[i] -lbl[i]-> dst[i] (duplicates allowed).
+ *   max_states      capacity of the outputs in DFA states (bottom included).
+ *   out_delta       host int32 [max_states*nlabels], state-major; out_accept host uint32 bitmap
+ *                   [(max_states+31)/32]; *out_n = number of DFA states.
+ * Numbering: subsets in the order a FIFO breadth-first search discovers them, labels taken in
+ * increasing order; {s0} is state 0; bottom is state *out_n - 1.
+ * Returns DFAMIN_EINVAL for an entry out of range, DFAMIN_ENOMEM (and *out_n = -1) when more
+ * than max_states states are needed.
+ */
+dfamin_status dfamin_lts_determinize(int32_t n, int32_t nlabels, int64_t m, const int32_t *src,
+                                     const int32_t *lbl, const int32_t *dst, int32_t s0,
+                                     int32_t max_states, int32_t *out_delta,
+                                     uint32_t *out_accept, int32_t *out_n);
+
 /* Text of the last CUDA runtime failure seen by the library on the calling thread ("" if
  * none); meant for diagnostics after DFAMIN_ECUDA / DFAMIN_ENOMEM.  Thread-local storage. */
 const char *dfamin_last_cuda_error(void);

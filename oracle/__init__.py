@@ -238,3 +238,38 @@ def minimal_dfa(delta, accept, n: int, k: int, q0: int):
     block, nb = hopcroft(rdelta, racc, cnt, k)
     qd, qa, q0m = quotient(rdelta, racc, cnt, k, block, nb, int(newid[q0]))
     return qd, qa, nb, q0m, cnt
+
+
+def lts_to_dfa(n: int, nlabels: int, src, lbl, dst, s0: int):
+    """LTS -> DFA as Sec. 4.1 describes it: the powerset construction from s0 (FIFO order of
+    discovery, labels in increasing order), every subset accepting, plus a non-accepting bottom
+    state that takes every missing transition.  Returns (nstates, delta, accept bitmap)."""
+    succ = {}
+    for s, a, t in zip(np.asarray(src).tolist(), np.asarray(lbl).tolist(),
+                       np.asarray(dst).tolist()):
+        succ.setdefault((s, a), set()).add(t)
+    start = frozenset([s0])
+    ids, order, rows = {start: 0}, [start], []
+    i = 0
+    while i < len(order):
+        S = order[i]
+        i += 1
+        row = []
+        for a in range(nlabels):
+            T = frozenset(t for s in S for t in succ.get((s, a), ()))
+            if not T:
+                row.append(None)
+                continue
+            if T not in ids:
+                ids[T] = len(order)
+                order.append(T)
+            row.append(ids[T])
+        rows.append(row)
+    bottom = len(order)
+    total = bottom + 1
+    delta = np.array([bottom if t is None else t for row in rows for t in row] +
+                     [bottom] * nlabels, dtype=np.int32)
+    acc = np.zeros((total + 31) // 32, np.uint32)
+    for q in range(bottom):
+        acc[q >> 5] |= np.uint32(1 << (q & 31))
+    return total, delta, acc

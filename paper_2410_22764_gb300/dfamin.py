@@ -48,6 +48,7 @@ ABI_FUNCTIONS = (
     "dfamin_quotient",
     "dfamin_minimal_dfa_workspace_size",
     "dfamin_minimal_dfa",
+    "dfamin_lts_determinize",
 )
 
 
@@ -106,6 +107,9 @@ def _load():
               lib.dfamin_quotient_workspace_size, lib.dfamin_quotient,
               lib.dfamin_minimal_dfa_workspace_size, lib.dfamin_minimal_dfa):
         f.restype = ctypes.c_int
+    lib.dfamin_lts_determinize.argtypes = [i32, i32, ctypes.c_int64, p, p, p, i32, i32, p, p,
+                                           ctypes.POINTER(i32)]
+    lib.dfamin_lts_determinize.restype = ctypes.c_int
     lib.dfamin_last_cuda_error.argtypes = []
     lib.dfamin_last_cuda_error.restype = ctypes.c_char_p
     for f in (lib.dfamin_minimize, lib.dfamin_workspace_size, lib.dfamin_minimize_ex):
@@ -318,6 +322,32 @@ def minimal_dfa(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, q0: i
     if rc:
         raise DfaminError(rc, "dfamin_minimal_dfa")
     return qd, qa, sc
+
+
+def lts_determinize(n: int, nlabels: int, src, lbl, dst, s0: int, max_states: int = 0):
+    """LTS -> DFA (host code, host arrays): powerset construction from s0, every subset
+    accepting, plus a non-accepting bottom state.  Returns (nstates, delta int32 [nstates*nlabels],
+    accept uint32 bitmap)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    lbl = np.ascontiguousarray(lbl, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    if not (src.size == lbl.size == dst.size):
+        raise ValueError("src, lbl and dst must have the same length")
+    cap = max_states or max(2, 2 * n + 1)
+    while True:
+        delta = np.empty(max(cap * nlabels, 1), np.int32)
+        acc = np.empty((cap + 31) // 32, np.uint32)
+        out_n = ctypes.c_int32(0)
+        pp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        rc = _lib.dfamin_lts_determinize(n, nlabels, src.size, pp(src), pp(lbl), pp(dst), s0, cap,
+                                         pp(delta), pp(acc), ctypes.byref(out_n))
+        if rc == ENOMEM and not max_states:
+            cap *= 4
+            continue
+        if rc:
+            raise DfaminError(rc, "dfamin_lts_determinize")
+        ns = out_n.value
+        return ns, delta[: ns * nlabels].copy(), acc[: (ns + 31) // 32].copy()
 
 
 def to_device(delta: np.ndarray, accept: np.ndarray, device="cuda"):

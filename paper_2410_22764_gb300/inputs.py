@@ -240,6 +240,29 @@ def bitsplitter_dfa_native(nbits: int, threads: int | None = None) -> Dfa:
     return Dfa(n, k, delta, accept)
 
 
+def lts_synthetic(n: int, nlabels: int, p_edge: float, p_nd: float, seed: int):
+    """A seeded LTS with bounded powerset growth, standing in for the VLTS inputs of Sec. 4.1.
+
+    A partial deterministic system on n states (edge s -a-> t present with probability p_edge,
+    t uniform) is doubled into states 0..2n-1 (state s + n mirrors s); each edge s -a-> t of
+    the first copy also gets, with probability p_nd, the nondeterministic alternative
+    s -a-> t + n.  Reachable subsets are singletons and mirror pairs {t, t + n}, so the DFA has at
+    most 3n + 1 states.  Returns (2n, src, lbl, dst) with int32 arrays."""
+    rng = np.random.default_rng(seed)
+    s = np.repeat(np.arange(n, dtype=np.int64), nlabels)
+    a = np.tile(np.arange(nlabels, dtype=np.int64), n)
+    keep = rng.random(s.size) < p_edge
+    s, a = s[keep], a[keep]
+    t = rng.integers(0, n, s.size)
+    nd = rng.random(s.size) < p_nd
+    src = np.concatenate([s, s + n, s[nd]])
+    lbl = np.concatenate([a, a, a[nd]])
+    dst = np.concatenate([t, t + n, t[nd] + n])
+    order = rng.permutation(src.size)
+    return (2 * n, src[order].astype(np.int32), lbl[order].astype(np.int32),
+            dst[order].astype(np.int32))
+
+
 def fig1_dfa() -> Dfa:
     """Fig. 1: q0 -a-> q1 -a-> ... -a-> q9, q9 loops on a and is the only accepting state."""
     delta = np.minimum(np.arange(10) + 1, 9).astype(np.int32)

@@ -129,3 +129,20 @@ def test_bad_entries(dm):
     assert sc.cpu().tolist() == [-dm.EINVAL, dm.EINVAL]
     # the context stays usable
     test_quotient_of_full_partition(dm)
+
+
+@pytest.mark.parametrize("n,L,seed", [(3000, 4, 1), (50000, 12, 2)])
+def test_lts_pipeline(dm, n, L, seed):
+    # synthetic LTS -> DFA (host front end) -> minimal DFA on the device, against the oracle's
+    # own front end and minimal DFA
+    nn, src, lbl, dst = I.lts_synthetic(n, L, 0.7, 0.2, seed)
+    ns, delta, acc = dm.lts_determinize(nn, L, src, lbl, dst, 0)
+    wns, wdelta, wacc = oracle.lts_to_dfa(nn, L, src, lbl, dst, 0)
+    assert ns == wns and np.array_equal(delta, wdelta)
+    wd, wa, wn, wq0, wr = oracle.minimal_dfa(wdelta, wacc, wns, L, 0)
+    dd, aa = dm.to_device(delta, acc)
+    qd, qa, sc = dm.minimal_dfa(ns, L, dd, aa, 0)
+    torch.cuda.synchronize()
+    got_n, got_q0, got_r, _, st = sc.cpu().tolist()
+    assert st == 0 and (got_n, got_q0, got_r) == (wn, wq0, wr)
+    assert np.array_equal(qd.cpu().numpy()[: wn * L], wd)
