@@ -47,6 +47,7 @@ struct BatchDesc {             // one DFA, in ticket order
     int32_t levels, sig_stride, max_passes;
     int32_t cta_base;          // first entry of its per-CTA counts
     int32_t nonid_base;        // first entry of its identity-letter flags
+    int32_t pat_base;          // first entry of its round-1 pattern minima, -1 = none
     int64_t o_block, o_lst_s, o_lst_slot, o_lst_rst, o_lead, o_lead_slot, o_stg, o_table, o_sig,
         o_cl, o_cl_letter, o_naive;
 };
@@ -65,6 +66,7 @@ struct BatchArgs {
     unsigned long long* ticket;    // zeroed per launch
     Ctrl* ctrl;                    // [count], zeroed per launch, indexed by the caller's index
     int32_t* nonid;                // zeroed per launch
+    int32_t* pat;                  // zeroed per launch: round-1 pattern minima of team DFAs
     int32_t* cta_cnt;
     uint32_t flags;
     int32_t algo;
@@ -85,6 +87,7 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.ctrl = A.ctrl + D.index;
     J.cta_cnt = A.cta_cnt + D.cta_base;
     J.nonid = A.nonid + D.nonid_base;
+    J.pat_rev = D.pat_base >= 0 ? A.pat + D.pat_base : nullptr;
     unsigned char* r = A.ws + D.region;
     J.cl_letter = (int32_t*)(r + D.o_cl_letter);
     J.block = (int32_t*)(r + D.o_block);
@@ -96,7 +99,7 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.stg = (int32_t*)(r + D.o_stg);
     J.naive_new = (int32_t*)(r + D.o_naive);
     J.algo = A.algo;
-    J.table = (uint32_t*)(r + D.o_table);
+    J.table = (unsigned long long*)(r + D.o_table);
     J.mask = D.cap - 1;
     J.sig = (int32_t*)(r + D.o_sig);
     J.sig_stride = D.sig_stride;
@@ -175,7 +178,7 @@ struct dfamin_batch_plan_s {
     int64_t tickets = 0;
     int grid = 0;
     size_t dsmem = 0;
-    size_t off_ctrl = 0, off_nonid = 0, zero_end = 0, off_cta = 0, ws_bytes = 0;
+    size_t off_ctrl = 0, off_nonid = 0, off_pat = 0, zero_end = 0, off_cta = 0, ws_bytes = 0;
     int64_t total_states = 0, total_delta = 0;
 };
 
@@ -286,7 +289,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
     const size_t A = 256;
     size_t off = 256;                                // [0, 256): ticket counter
     P->off_ctrl = off; off = align_up(off + sizeof(Ctrl) * (size_t)count, A);
-    int64_t ksum = 0, team_sum = 0;
+    int64_t ksum = 0, team_sum = 0, patsum = 0;
     P->desc.resize(count);
     for (int32_t j = 0; j < count; ++j) {
         const int32_t i = order[j];
@@ -306,6 +309,11 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
         D.cta_base = (int32_t)(team_sum - D.team);
         D.nonid_base = (int32_t)ksum;
         ksum += std::max(1, D.k);
+        D.pat_base = -1;
+        if (!D.small && !closure && D.k >= 1 && D.k <= kPatMaxK) {
+            D.pat_base = (int32_t)patsum;
+            patsum += 1 << (D.k + 1);
+        }
         D.max_passes = o.max_passes > 0 ? o.max_passes : (D.n < 0x7fffffff ? D.n + 1 : D.n);
         if (D.small) small_smem_bytes(D.n, &D.small_cap);
     }
@@ -317,6 +325,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
         for (auto& D : P->desc) D.delta_off = doff[D.index];
     }
     P->off_nonid = off; off = align_up(off + sizeof(int32_t) * (size_t)ksum, A);
+    P->off_pat = off; off = align_up(off + sizeof(int32_t) * (size_t)std::max<int64_t>(1, patsum), A);
     P->zero_end = off;
     P->off_cta = off; off = align_up(off + sizeof(int32_t) * (size_t)team_sum, A);
     for (auto& D : P->desc) {
@@ -434,6 +443,7 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
     A.ticket = (unsigned long long*)base;
     A.ctrl = (Ctrl*)(base + plan->off_ctrl);
     A.nonid = (int32_t*)(base + plan->off_nonid);
+    A.pat = (int32_t*)(base + plan->off_pat);
     A.cta_cnt = (int32_t*)(base + plan->off_cta);
     A.flags = plan->opt.flags & ~DFAMIN_FLAG_TRACE;
     A.algo = plan->opt.algorithm;

@@ -122,7 +122,7 @@ namespace {
 
 // Workspace of one DFA: [control | per-CTA counts | identity flags | DFA arrays | trace].
 struct Layout {
-    size_t ctrl, cta_cnt, nonid, zero_end;  // [ctrl .. zero_end) is zeroed per launch
+    size_t ctrl, cta_cnt, nonid, pat, zero_end;  // [ctrl .. zero_end) is zeroed per launch
     size_t trace, dfa, total;
     DfaLayout d;
 };
@@ -135,6 +135,7 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
     L.ctrl = off; off = align_up(off + sizeof(Ctrl), A);
     L.cta_cnt = off; off = align_up(off + sizeof(int32_t) * kMaxCtas, A);
     L.nonid = off; off = align_up(off + sizeof(int32_t) * (size_t)(k > 0 ? k : 1), A);
+    L.pat = off; off = align_up(off + sizeof(int32_t) * (size_t)kPatMax, A);
     L.zero_end = off;
     L.dfa = off;
     L.d = make_dfa_layout(n, k, o.closure == DFAMIN_CLOSURE_ON, true);
@@ -186,7 +187,7 @@ void bind_dfa_arrays(Job& J, unsigned char* region, const DfaLayout& d)
     J.lead_slot = (uint32_t*)(region + d.lead_slot);
     J.stg = (int32_t*)(region + d.stg);
     J.naive_new = (int32_t*)(region + d.naive_new);
-    J.table = (uint32_t*)(region + d.table);
+    J.table = (unsigned long long*)(region + d.table);
     J.mask = d.cap - 1;
     J.sig = (int32_t*)(region + d.sig);
     J.sig_stride = d.sig_stride;
@@ -228,6 +229,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.ctrl = (Ctrl*)(base + L.ctrl);
     J.cta_cnt = (int32_t*)(base + L.cta_cnt);
     J.nonid = (int32_t*)(base + L.nonid);
+    J.pat_rev = (int32_t*)(base + L.pat);
     bind_dfa_arrays(J, base + L.dfa, L.d);
     J.max_passes = o.max_passes > 0 ? o.max_passes : (n < 0x7fffffff ? n + 1 : n);
     J.flags = o.flags;

@@ -78,7 +78,7 @@ inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays
         L.lead_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
         L.stg = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
         L.naive_new = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
-        L.table = off; off = align_up(off + sizeof(uint32_t) * (size_t)L.cap, A);
+        L.table = off; off = align_up(off + sizeof(unsigned long long) * (size_t)L.cap, A);
         L.sig = off;
         off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);
     }

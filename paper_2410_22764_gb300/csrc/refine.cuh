@@ -56,6 +56,8 @@ constexpr int kTeamThreads = DFAMIN_TEAM_THREADS;
 constexpr int kMaxCtas = 8192;            // capacity of the per-CTA count array
 constexpr int64_t kBarrierTimeoutNs = 4000000000ll;        // 4 s per CTA barrier
 constexpr int kSmallMaxStates = 8192;     // largest n for the shared-memory kernel
+constexpr int kPatMaxK = 8;               // round 1 from acceptance bits for k <= kPatMaxK
+constexpr int kPatMax = 1 << (kPatMaxK + 1);
 
 // ------------------------------------------------------------------------------------------
 // Device state
@@ -84,7 +86,7 @@ struct Job {
     int32_t* cl;                         // closure columns [ncl_letters*(levels-1)][n]
     int32_t* cl_letter;                  // [k] letters with closure columns (compacted)
     int32_t* nonid;                      // [k] 1 if letter is not the identity
-    uint32_t* table;                     // [mask+1] group slots (smallest state), kEmpty
+    unsigned long long* table;           // [cap] group table: (min state << 32) | representative
     int32_t* sig;                        // [n * sig_stride] signature rows
     int32_t sig_stride;                  // ints per row, multiple of 4, >= ncols + 1
     int32_t* lst_s;                      // [n] changed states, per-CTA segments
@@ -102,6 +104,8 @@ struct Job {
     int64_t timeout_ns;
     long long* trace;                    // phase trace or null
     long long trace_cap;                 // records
+    int32_t* pat_rev;                    // [kPatMax] round-1 pattern minima (n - state), zeroed
+                                         // per launch; null = round 1 by the general path
     int32_t algo;                        // DFAMIN_ALG_SIGNATURE or DFAMIN_ALG_LEADER
     int32_t* naive_new;                  // [n] leader mode: elected new leader per old leader
 };
@@ -327,6 +331,18 @@ static __device__ int cta_min(int v)
 // ------------------------------------------------------------------------------------------
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr uint32_t kFail = 0xffffffffu;
+// A group-table slot holds (smallest member << 32) | representative.  The representative is the
+// state that claimed the slot; its row is the one members compare against, and it never
+// changes during a round, so only claimers publish rows.  atomicMin on the whole word lowers
+// the smallest member and keeps the representative (every member passes the same low half).
+constexpr unsigned long long kEmptySlot = ~0ull;
+
+static __device__ __forceinline__ unsigned long long slot_word(int min_state, int rep)
+{
+    return ((unsigned long long)(uint32_t)min_state << 32) | (uint32_t)rep;
+}
+static __device__ __forceinline__ int slot_min(unsigned long long w) { return (int)(w >> 32); }
+static __device__ __forceinline__ int slot_rep(unsigned long long w) { return (int)(uint32_t)w; }
 
 static __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
 {
@@ -412,9 +428,9 @@ static __device__ __forceinline__ void publish_row(const Job& J, int s, const in
     __threadfence();
 }
 
-// Insert s into the table; returns the slot of s's group.  A slot holds a state of its group:
-// it is claimed by CAS from empty and lowered to the group's smallest state by atomicMin.  A
-// state's row is published only when it becomes a slot holder, so ordinary members write
+// Insert s into the table; returns the slot of s's group.  A slot is claimed by CAS from empty
+// by a state that published its row first (the representative); a member whose full row equals
+// the representative's lowers the slot's smallest member by atomicMin.  Ordinary members write
 // nothing.  Equality is decided on the full rows, never on the hash.
 template <int SS>
 static __device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int (&row)[SS],
@@ -423,26 +439,23 @@ static __device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int
     uint32_t idx = (uint32_t)h & J.mask;
     bool published = false;
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
-        uint32_t w = ld_acquire_u32(&J.table[idx]);
-        if (w == kEmpty) {
+        unsigned long long w = ld_acquire_u64(&J.table[idx]);
+        if (w == kEmptySlot) {
             if (!published) { publish_row<SS>(J, s, row); published = true; }
-            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
-            if (w == kEmpty) {
+            w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, s));
+            if (w == kEmptySlot) {
                 atomicAdd(s_claims, 1);
                 return idx;
             }
-            __threadfence();   // acquire: w's row was published before w entered the slot
+            __threadfence();   // acquire: the representative's row was published before its CAS
         }
         int tr[SS];
-        load_row<SS>(J.sig, (int)w, tr);
+        load_row<SS>(J.sig, slot_rep(w), tr);
         bool eq = true;
 #pragma unroll
         for (int c = 0; c < SS; ++c) eq &= (tr[c] == row[c]);
         if (eq) {
-            if ((uint32_t)s < w) {
-                if (!published) { publish_row<SS>(J, s, row); published = true; }
-                atomicMin(&J.table[idx], (uint32_t)s);
-            }
+            if (s < slot_min(w)) atomicMin(&J.table[idx], slot_word(s, slot_rep(w)));
             return idx;
         }
         idx = (idx + 1) & J.mask;
@@ -485,17 +498,18 @@ static __device__ uint32_t insert_row_generic(const Job& J, int s, int head, uin
     uint32_t idx = (uint32_t)h & J.mask;
     bool published = false;
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
-        uint32_t w = ld_acquire_u32(&J.table[idx]);
-        if (w == kEmpty) {
+        unsigned long long w = ld_acquire_u64(&J.table[idx]);
+        if (w == kEmptySlot) {
             if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
-            w = atomicCAS(&J.table[idx], kEmpty, (uint32_t)s);
-            if (w == kEmpty) {
+            w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, s));
+            if (w == kEmptySlot) {
                 atomicAdd(s_claims, 1);
                 return idx;
             }
             __threadfence();
         }
-        const int4* theirs = reinterpret_cast<const int4*>(J.sig + (int64_t)w * J.sig_stride);
+        const int4* theirs =
+            reinterpret_cast<const int4*>(J.sig + (int64_t)slot_rep(w) * J.sig_stride);
         bool eq = true;
         for (int v = 0; v < nch && eq; ++v) {
             int x[4];
@@ -504,10 +518,7 @@ static __device__ uint32_t insert_row_generic(const Job& J, int s, int head, uin
             eq = x[0] == b.x && x[1] == b.y && x[2] == b.z && x[3] == b.w;
         }
         if (eq) {
-            if ((uint32_t)s < w) {
-                if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
-                atomicMin(&J.table[idx], (uint32_t)s);
-            }
+            if (s < slot_min(w)) atomicMin(&J.table[idx], slot_word(s, slot_rep(w)));
             return idx;
         }
         idx = (idx + 1) & J.mask;
@@ -951,79 +962,145 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     const bool closure = J.levels > 1;
     const bool elide = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY);
     int passes = 0;
+    bool round1_done = false;
+    int round1_count0 = 0, round1_count1 = 0;
     const bool tw = rank == 0 && threadIdx.x == 0;     // trace writer
     if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
     trace_mark(J, tw, 0, 0);
 
-    // ---- phase V: validate delta rows, find the two initial leaders, mark identity letters,
-    //      empty this CTA's slice of the hash table
-    {
-        bool bad = false;
-        const int64_t r0 = (int64_t)c0 * k, r1 = (int64_t)c1 * k;
-        if (!closure && n > 2) {
-            // validated in round 1 (row_ok / row_chunk)
-        } else if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
-            const int64_t v0 = r0 / 4, v1 = r1 / 4;   // r0 is a multiple of 4 (chunk % 32 == 0)
-            const int4* d4 = reinterpret_cast<const int4*>(J.delta);
-            for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
-                const int4 v = __ldcs(d4 + i);
-                bad |= ((unsigned)v.x >= (unsigned)n) | ((unsigned)v.y >= (unsigned)n) |
-                       ((unsigned)v.z >= (unsigned)n) | ((unsigned)v.w >= (unsigned)n);
+    // ---- round 1 from the acceptance bits.  In P0 = {F, Q\F} a state's signature is fixed by
+    //      the acceptance of the state and of its k successors, so round 1 groups the states by
+    //      that (k+1)-bit pattern (exact: the pattern is the signature written in bits), and a
+    //      group's id is its smallest state (per-CTA minima in shared memory, then one atomic per
+    //      CTA and pattern).  It replaces phases V and I and the general round 1, with the same
+    //      partition and pass count.
+    if constexpr (KC > 0 && KC <= kPatMaxK) {
+        if (J.pat_rev && !closure && J.algo == DFAMIN_ALG_SIGNATURE) {
+            constexpr int NP = 1 << (KC + 1);
+            __shared__ int s_pat[NP];
+            for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = 0x7fffffff;
+            __syncthreads();
+            bool bad = false;
+            for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+                int r[KC];
+                load_succ<KC>(J.delta, q, r);
+                int pat = is_accepting(J, q) ? 1 : 0;
+#pragma unroll
+                for (int c = 0; c < KC; ++c) {
+                    if ((unsigned)r[c] >= (unsigned)n) bad = true;
+                    else pat |= (is_accepting(J, r[c]) ? 1 : 0) << (c + 1);
+                }
+                J.block[q] = pat;                     // the pattern, until the ids are known
+                if (q < s_pat[pat]) atomicMin(&s_pat[pat], q);
             }
-            for (int64_t i = v1 * 4 + threadIdx.x; i < r1; i += blockDim.x)
-                bad |= (unsigned)__ldcs(&J.delta[i]) >= (unsigned)n;
-        } else {
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-                const int v = __ldcs(&J.delta[i]);
-                if ((unsigned)v >= (unsigned)n) bad = true;
-                if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
+            if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
+            const uint64_t cap = (uint64_t)J.mask + 1;
+            const uint64_t per = (cap + T - 1) / T;
+            const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
+            for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmptySlot;
+            __syncthreads();
+            for (int i = threadIdx.x; i < NP; i += blockDim.x)
+                if (s_pat[i] != 0x7fffffff) atomicMax(&J.pat_rev[i], n - s_pat[i]);
+            if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, 1, 5);
+            for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = ld_volatile(&J.pat_rev[i]);
+            __syncthreads();
+            for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) J.block[q] = n - s_pat[J.block[q]];
+            int c1cnt = 0, has_f = 0, has_n = 0;
+            for (int i = 0; i < NP; ++i) {
+                if (s_pat[i] > 0) {
+                    ++c1cnt;
+                    if (i & 1) has_f = 1; else has_n = 1;
+                }
             }
-        }
-        if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
-        int mf = 0x7fffffff, mn = 0x7fffffff;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-            if (is_accepting(J, s)) mf = min(mf, s); else mn = min(mn, s);
-        }
-        mf = cta_min(mf);
-        mn = cta_min(mn);
-        if (threadIdx.x == 0) {
-            if (mf != 0x7fffffff) atomicMax(&J.ctrl->min_f_rev, n - mf);
-            if (mn != 0x7fffffff) atomicMax(&J.ctrl->min_n_rev, n - mn);
-        }
-        const uint64_t cap = (uint64_t)J.mask + 1;
-        const uint64_t per = (cap + T - 1) / T;
-        const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
-        for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmpty;
-        if (J.algo == DFAMIN_ALG_LEADER)
-            for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) J.naive_new[i] = 0x7fffffff;
-    }
-    if (!team_barrier(ts)) goto done;
-    trace_mark(J, tw, 0, 1);
-
-    // ---- phase I: initial partition P0 = {F, Q\F} as leader ids
-    {
-        const int rf = ld_volatile(&J.ctrl->min_f_rev), rn = ld_volatile(&J.ctrl->min_n_rev);
-        const int lf = n - rf, ln = n - rn;
-        for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
-            J.block[s] = is_accepting(J, s) ? lf : ln;
-        if (rank == 0 && threadIdx.x == 0) {
-            int m = 0;
-            if (rf > 0) J.lead[m++] = lf;
-            if (rn > 0) J.lead[m++] = ln;
-            J.ctrl->nlead = m;
-        }
-        if (closure && rank == 0 && threadIdx.x == 0) {
-            int m = 0;
-            for (int a = 0; a < k; ++a)
-                if (!elide || ld_volatile(&J.nonid[a])) J.cl_letter[m++] = a;
-            J.ctrl->ncl_letters = m;
+            if (rank == 0 && threadIdx.x == 0) {
+                int m = 0;
+                for (int i = 0; i < NP; ++i)
+                    if (s_pat[i] > 0) J.lead[m++] = n - s_pat[i];
+                J.ctrl->nlead = m;
+            }
+            round1_count0 = has_f + has_n;
+            round1_count1 = c1cnt;
+            if (!team_barrier(ts)) goto done;
+            trace_mark(J, tw, 1, 6);
+            round1_done = true;
         }
     }
-    if (!team_barrier(ts)) goto done;
-    trace_mark(J, tw, 0, 2);
+    if (!round1_done) {
+        // ---- phase V: validate delta rows, find the two initial leaders, mark identity letters,
+        //      empty this CTA's slice of the hash table
+        {
+            bool bad = false;
+            const int64_t r0 = (int64_t)c0 * k, r1 = (int64_t)c1 * k;
+            if (!closure && n > 2) {
+                // validated in round 1 (row_ok / row_chunk)
+            } else if (!closure && ((uintptr_t)J.delta & 15u) == 0) {
+                const int64_t v0 = r0 / 4, v1 = r1 / 4;   // r0 is a multiple of 4 (chunk % 32 == 0)
+                const int4* d4 = reinterpret_cast<const int4*>(J.delta);
+                for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
+                    const int4 v = __ldcs(d4 + i);
+                    bad |= ((unsigned)v.x >= (unsigned)n) | ((unsigned)v.y >= (unsigned)n) |
+                           ((unsigned)v.z >= (unsigned)n) | ((unsigned)v.w >= (unsigned)n);
+                }
+                for (int64_t i = v1 * 4 + threadIdx.x; i < r1; i += blockDim.x)
+                    bad |= (unsigned)__ldcs(&J.delta[i]) >= (unsigned)n;
+            } else {
+                for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                    const int v = __ldcs(&J.delta[i]);
+                    if ((unsigned)v >= (unsigned)n) bad = true;
+                    if (closure && v != (int)(i / k)) J.nonid[i % k] = 1;
+                }
+            }
+            if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
+            int mf = 0x7fffffff, mn = 0x7fffffff;
+            for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
+                if (is_accepting(J, s)) mf = min(mf, s); else mn = min(mn, s);
+            }
+            mf = cta_min(mf);
+            mn = cta_min(mn);
+            if (threadIdx.x == 0) {
+                if (mf != 0x7fffffff) atomicMax(&J.ctrl->min_f_rev, n - mf);
+                if (mn != 0x7fffffff) atomicMax(&J.ctrl->min_n_rev, n - mn);
+            }
+            const uint64_t cap = (uint64_t)J.mask + 1;
+            const uint64_t per = (cap + T - 1) / T;
+            const uint64_t t0 = min(cap, per * rank), t1 = min(cap, t0 + per);
+            for (uint64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) J.table[i] = kEmptySlot;
+            if (J.algo == DFAMIN_ALG_LEADER)
+                for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) J.naive_new[i] = 0x7fffffff;
+        }
+        if (!team_barrier(ts)) goto done;
+        trace_mark(J, tw, 0, 1);
+
+        // ---- phase I: initial partition P0 = {F, Q\F} as leader ids
+        {
+            const int rf = ld_volatile(&J.ctrl->min_f_rev), rn = ld_volatile(&J.ctrl->min_n_rev);
+            const int lf = n - rf, ln = n - rn;
+            for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x)
+                J.block[s] = is_accepting(J, s) ? lf : ln;
+            if (rank == 0 && threadIdx.x == 0) {
+                int m = 0;
+                if (rf > 0) J.lead[m++] = lf;
+                if (rn > 0) J.lead[m++] = ln;
+                J.ctrl->nlead = m;
+            }
+            if (closure && rank == 0 && threadIdx.x == 0) {
+                int m = 0;
+                for (int a = 0; a < k; ++a)
+                    if (!elide || ld_volatile(&J.nonid[a])) J.cl_letter[m++] = a;
+                J.ctrl->ncl_letters = m;
+            }
+        }
+        if (!team_barrier(ts)) goto done;
+        trace_mark(J, tw, 0, 2);
+    }
 
     {
-        int count = (ld_volatile(&J.ctrl->min_f_rev) > 0) + (ld_volatile(&J.ctrl->min_n_rev) > 0);
+        int count = round1_done ? round1_count1
+                                : (ld_volatile(&J.ctrl->min_f_rev) > 0) +
+                                      (ld_volatile(&J.ctrl->min_n_rev) > 0);
+        // a discrete P0 (n <= 2) needs no round at all, as in the general path
+        if (round1_done) passes = round1_count0 < n ? 1 : 0;
         int ncl_cols = 0;
         if constexpr (KC == 0) {
             // ---- closure levels (Alg. transPR)
@@ -1039,7 +1116,9 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         const bool leader_mode = J.algo == DFAMIN_ALG_LEADER;
         // signature rounds stop early once every block is a singleton; Alg. 2 runs until a
         // round changes nothing
-        while (leader_mode || count < n) {
+        // round 1 done above and nothing split: stable after one pass
+        const bool stable1 = round1_done && round1_count1 == round1_count0;
+        while (!stable1 && (leader_mode || count < n)) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
                 break;
@@ -1052,7 +1131,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 const int gid = rank * (int)blockDim.x + (int)threadIdx.x;
                 for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x) {
                     if (leader_mode) J.naive_new[__ldcg(&J.lead_slot[i])] = 0x7fffffff;
-                    else J.table[__ldcg(&J.lead_slot[i])] = kEmpty;
+                    else J.table[__ldcg(&J.lead_slot[i])] = kEmptySlot;
                 }
                 lead_reset_from = nlead;
                 phase_leaders<KC>(J, rank, T, nlead, ncols);
@@ -1102,7 +1181,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                         for (int ci = threadIdx.x; ci < CtaCache<RowOf<KC>::SS>::kSlots;
                              ci += blockDim.x)
                             if (cache.gslot[ci] != kEmpty)
-                                cache.gmin[ci] = (int)ld_relaxed_u32(&J.table[cache.gslot[ci]]);
+                                cache.gmin[ci] = slot_min(__ldcg(&J.table[cache.gslot[ci]]));
                         __syncthreads();
                     }
                     // software pipeline: the next entry's (state, slot) is loaded ahead
@@ -1130,7 +1209,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                 gs = cache.gslot[ci];
                             } else {
                                 m = leader_mode ? ld_volatile(&J.naive_new[slot])
-                                                : (int)ld_relaxed_u32(&J.table[slot]);
+                                                : slot_min(__ldcg(&J.table[slot]));
                                 gs = slot;
                             }
                             J.block[s] = m;
@@ -1148,7 +1227,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                             s = J.lst_s[c0 + i];
                             gs = J.lst_slot[c0 + i];
                             const int m = leader_mode ? ld_volatile(&J.naive_new[gs])
-                                                      : (int)ld_relaxed_u32(&J.table[gs]);
+                                                      : slot_min(__ldcg(&J.table[gs]));
                             J.block[s] = m;
                             lead = (m == s);
                         }

@@ -272,3 +272,14 @@ def test_closure_saturation_mixed_letters(dm):
     check_leader(dm, d, closure=True)
     lv, _ = closure_levels_built(dm, d)
     assert lv == int(np.log2(n))          # letter 0 needs every level
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 9])
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 257, 5000])
+def test_team_kernel_tiny_and_pattern_round(dm, n, k):
+    # the multi-CTA kernel on tiny DFAs (round 1 from acceptance patterns for k <= 8, the
+    # general round 1 for k = 9), including all-accepting and all-rejecting DFAs
+    for p in (0.5, 0.0, 1.0):
+        d = I.random_dfa(n, k, p, 77 * n + k)
+        for ctas in (0, 3):
+            check(dm, d, ctas=ctas, smem_states=1)
