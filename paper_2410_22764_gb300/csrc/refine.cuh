@@ -415,10 +415,26 @@ __device__ __forceinline__ bool row_ok(const Job& J, const int (&r)[KC])
     return ok;
 }
 
+// Row layout of the compile-time-width kernels: the successors' block ids first, then the head
+// (the state's own block id), zero padding to SS ints:  [b_0 .. b_{KC-1}, head, 0 ..].  A member
+// compares its successors' ids with its leader's (the heads are equal by definition), which
+// reads only the first NB int4 of the leader's row: one 16-byte load for KC <= 4.
 template <int KC>
 struct RowOf {
     static constexpr int SS = (KC + 1 + 3) / 4 * 4;
+    static constexpr int NB = (KC + 3) / 4;
 };
+
+template <int SS, int NB>
+static __device__ __forceinline__ void load_row_prefix(const int32_t* sig, int s, int (&row)[SS])
+{
+    const int4* p = reinterpret_cast<const int4*>(sig + (int64_t)s * SS);
+#pragma unroll
+    for (int v = 0; v < NB; ++v) {
+        const int4 x = __ldcg(p + v);
+        row[4 * v] = x.x; row[4 * v + 1] = x.y; row[4 * v + 2] = x.z; row[4 * v + 3] = x.w;
+    }
+}
 
 // Publish s's row (the table may point other states at it) before s enters a slot.
 template <int SS>
@@ -642,21 +658,21 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
 #pragma unroll
                 for (int c = 0; c < SS; ++c) lr[c] = C.lrow[li][c];
             } else {
-                load_row<SS>(J.sig, L, lr);
+                load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
                 lfill = true;
             }
-            row[0] = L;
 #pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
+            for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
+            row[KC] = L;
 #pragma unroll
             for (int c = KC + 1; c < SS; ++c) row[c] = 0;
             bool same = true;
 #pragma unroll
-            for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
+            for (int c = 0; c < KC; ++c) same &= (row[c] == lr[c]);
             if (!same) {
                 h = hash_begin(L);
 #pragma unroll
-                for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
+                for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
                 h = hash_final(h, L, J.flags);
                 const int ci = (int)(h & (uint64_t)(kSlots - 1));
                 bool hit = false;
@@ -720,9 +736,9 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
             }
             if (!row_ok<KC>(J, r)) continue;
             int row[SS];
-            row[0] = s;
 #pragma unroll
-            for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
+            for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
+            row[KC] = s;
 #pragma unroll
             for (int c = KC + 1; c < SS; ++c) row[c] = 0;
             store_row<SS>(J.sig, s, row);
@@ -772,23 +788,23 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             uint32_t slot = 0;
             if (s < c1 && L != s && row_ok<KC>(J, r)) {
                 int lr[SS];
-                load_row<SS>(J.sig, L, lr);
+                load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
                 int row[SS];
-                row[0] = L;
 #pragma unroll
-                for (int c = 0; c < KC; ++c) row[1 + c] = ld_blk(&J.block[r[c]]);
+                for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
+                row[KC] = L;
 #pragma unroll
                 for (int c = KC + 1; c < SS; ++c) row[c] = 0;
                 bool same = true;
 #pragma unroll
-                for (int c = 1; c <= KC; ++c) same &= (row[c] == lr[c]);
+                for (int c = 0; c < KC; ++c) same &= (row[c] == lr[c]);
                 if (!same && J.algo == DFAMIN_ALG_LEADER) {
                     slot = naive_elect(J, s, L);
                     moved = true;
                 } else if (!same) {                   // T(s) != T(leader): regroup
                     uint64_t h = hash_begin(L);
 #pragma unroll
-                    for (int c = 1; c <= KC; ++c) h = hash_step(h, row[c]);
+                    for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
                     h = hash_final(h, L, J.flags);
                     slot = insert_row<SS>(J, s, h, row, s_claims);
                     moved = slot != kFail;
