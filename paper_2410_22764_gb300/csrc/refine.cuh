@@ -978,8 +978,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     const bool closure = J.levels > 1;
     const bool elide = !(J.flags & DFAMIN_FLAG_KEEP_IDENTITY);
     int passes = 0;
-    bool round1_done = false;
-    int round1_count0 = 0, round1_count1 = 0;
+    bool round1_done = false, round2_done = false;
+    int round1_count0 = 0, round1_count1 = 0, round1_count2 = 0;
     const bool tw = rank == 0 && threadIdx.x == 0;     // trace writer
     if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
     trace_mark(J, tw, 0, 0);
@@ -1007,6 +1007,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     else pat |= (is_accepting(J, r[c]) ? 1 : 0) << (c + 1);
                 }
                 J.block[q] = pat;                     // the pattern, until the ids are known
+                J.naive_new[q] = pat;                 // kept for a dense round 2
                 if (q < s_pat[pat]) atomicMin(&s_pat[pat], q);
             }
             if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
@@ -1040,6 +1041,68 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, 1, 6);
             round1_done = true;
+
+            // ---- round 2 by dense codes.  After round 1 a block is a (k+1)-bit pattern, so a
+            //      state's round-2 signature is exactly the code formed by the patterns of the
+            //      state and its successors ((k+1)^2 bits).  For k <= 4 the code indexes a
+            //      direct table (the group table's memory seen as 32-bit words, all ones = empty):
+            //      one atomicMin per state gives every group its smallest state, with no hashing
+            //      and no row comparison.  Same partition and pass count as the general round.
+            constexpr int PB = KC + 1;
+            if constexpr (PB * PB <= 26) {
+                const uint64_t words = 2ull * ((uint64_t)J.mask + 1);
+                if (round1_count1 != round1_count0 && round1_count1 < n && J.max_passes >= 2 &&
+                    (1ull << (PB * PB)) <= words) {
+                    uint32_t* dtab = reinterpret_cast<uint32_t*>(J.table);
+                    const int32_t* pidx = J.naive_new;
+                    if (threadIdx.x == 0) s_claims = 0;
+                    __syncthreads();
+                    int mine = 0;
+                    for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+                        int r[KC];
+                        load_succ<KC>(J.delta, q, r);
+                        uint32_t code = (uint32_t)__ldcs(&pidx[q]);
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) code = (code << PB) | (uint32_t)ld_blk(&pidx[r[c]]);
+                        J.lst_slot[q] = code;
+                        if (atomicMin(&dtab[code], (uint32_t)q) == 0xffffffffu) ++mine;
+                    }
+                    mine = cta_sum(mine);
+                    if (threadIdx.x == 0) {
+                        if (mine) atomicAdd(&J.ctrl->claims, (unsigned long long)mine);
+                        if (rank == 0) J.ctrl->nlead = 0;    // the list is rebuilt below
+                    }
+                    if (!team_barrier(ts)) goto done;
+                    trace_mark(J, tw, 2, 5);
+                    round1_count2 = (int)ld_acquire_u64(&J.ctrl->claims);
+                    // every group's smallest state leads it and lists its table word for reset
+                    if (threadIdx.x == 0) s_rst = 0;
+                    __syncthreads();
+                    for (int b = c0; b < c1; b += blockDim.x) {
+                        const int q = b + (int)threadIdx.x;
+                        bool lead = false;
+                        uint32_t code = 0;
+                        if (q < c1) {
+                            code = __ldcs(&J.lst_slot[q]);
+                            const int m = (int)__ldcg(&dtab[code]);
+                            J.block[q] = m;
+                            lead = m == q;
+                        }
+                        append_pair(J, c0, &s_rst, lead, q, code >> 1);
+                    }
+                    __syncthreads();
+                    const int nnew = s_rst;
+                    if (threadIdx.x == 0) s_base = nnew ? atomicAdd(&J.ctrl->nlead, nnew) : 0;
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < nnew; i += blockDim.x) {
+                        J.lead[s_base + i] = J.stg[c0 + i];
+                        J.lead_slot[s_base + i] = J.lst_rst[c0 + i];
+                    }
+                    if (!team_barrier(ts)) goto done;
+                    trace_mark(J, tw, 2, 6);
+                    round2_done = true;
+                }
+            }
         }
     }
     if (!round1_done) {
@@ -1112,11 +1175,13 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     }
 
     {
-        int count = round1_done ? round1_count1
-                                : (ld_volatile(&J.ctrl->min_f_rev) > 0) +
-                                      (ld_volatile(&J.ctrl->min_n_rev) > 0);
+        int count = round2_done   ? round1_count2
+                    : round1_done ? round1_count1
+                                  : (ld_volatile(&J.ctrl->min_f_rev) > 0) +
+                                        (ld_volatile(&J.ctrl->min_n_rev) > 0);
         // a discrete P0 (n <= 2) needs no round at all, as in the general path
         if (round1_done) passes = round1_count0 < n ? 1 : 0;
+        if (round2_done) passes = 2;
         int ncl_cols = 0;
         if constexpr (KC == 0) {
             // ---- closure levels (Alg. transPR)
@@ -1127,13 +1192,16 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         }
         const int ncols = k + ncl_cols;
         const int max_passes = J.max_passes;
-        unsigned long long claims_seen = 0;
-        int lead_reset_from = ld_volatile(&J.ctrl->nlead);   // initial leaders own no slot
+        unsigned long long claims_seen = round2_done ? (unsigned long long)round1_count2 : 0ull;
+        // leaders of the first rounds own no group slot, except after the dense round 2,
+        // whose every leader lists the table word it used
+        int lead_reset_from = round2_done ? 0 : ld_volatile(&J.ctrl->nlead);
         const bool leader_mode = J.algo == DFAMIN_ALG_LEADER;
         // signature rounds stop early once every block is a singleton; Alg. 2 runs until a
         // round changes nothing
-        // round 1 done above and nothing split: stable after one pass
-        const bool stable1 = round1_done && round1_count1 == round1_count0;
+        // round 1 (or 2) done above and nothing split: stable
+        const bool stable1 = (round1_done && round1_count1 == round1_count0) ||
+                             (round2_done && round1_count2 == round1_count1);
         while (!stable1 && (leader_mode || count < n)) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
@@ -1200,38 +1268,43 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                 cache.gmin[ci] = slot_min(__ldcg(&J.table[cache.gslot[ci]]));
                         __syncthreads();
                     }
-                    // software pipeline: the next entry's (state, slot) is loaded ahead
-                    int ns = 0;
-                    uint32_t nslot = 0;
-                    if ((int)threadIdx.x < cnt) {
-                        ns = __ldcs(&J.lst_s[c0 + threadIdx.x]);
-                        nslot = __ldcs(&J.lst_slot[c0 + threadIdx.x]);
-                    }
-                    for (int b = 0; b < cnt; b += blockDim.x) {
-                        const int i = b + threadIdx.x;
-                        const int s = ns;
-                        const uint32_t slot = nslot;
-                        if (i + (int)blockDim.x < cnt) {
-                            ns = __ldcs(&J.lst_s[c0 + i + blockDim.x]);
-                            nslot = __ldcs(&J.lst_slot[c0 + i + blockDim.x]);
-                        }
-                        bool lead = false;
-                        uint32_t gs = 0;
-                        if (i < cnt) {
-                            int m;
-                            if (use_cache && (slot & kCached)) {
-                                const int ci = (int)(slot & ~kCached);
-                                m = cache.gmin[ci];
-                                gs = cache.gslot[ci];
-                            } else {
-                                m = leader_mode ? ld_volatile(&J.naive_new[slot])
-                                                : slot_min(__ldcg(&J.table[slot]));
-                                gs = slot;
+                    // four entries per thread per step: their group-table reads are
+                    // independent and in flight together
+                    for (int b = 0; b < cnt; b += 4 * (int)blockDim.x) {
+                        int sv[4];
+                        uint32_t slv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int i = b + u * (int)blockDim.x + (int)threadIdx.x;
+                            sv[u] = -1;
+                            slv[u] = 0;
+                            if (i < cnt) {
+                                sv[u] = __ldcs(&J.lst_s[c0 + i]);
+                                slv[u] = __ldcs(&J.lst_slot[c0 + i]);
                             }
-                            J.block[s] = m;
-                            lead = (m == s);
                         }
-                        append_pair(J, c0, &s_rst, lead, s, gs);
+                        int mv[4];
+                        uint32_t gsv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            mv[u] = 0;
+                            gsv[u] = slv[u];
+                            if (sv[u] < 0) continue;
+                            if (use_cache && (slv[u] & kCached)) {
+                                const int ci = (int)(slv[u] & ~kCached);
+                                mv[u] = cache.gmin[ci];
+                                gsv[u] = cache.gslot[ci];
+                            } else {
+                                mv[u] = leader_mode ? ld_volatile(&J.naive_new[slv[u]])
+                                                    : slot_min(__ldcg(&J.table[slv[u]]));
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (sv[u] >= 0) J.block[sv[u]] = mv[u];
+                            append_pair(J, c0, &s_rst, sv[u] >= 0 && mv[u] == sv[u], sv[u],
+                                        gsv[u]);
+                        }
                     }
                 } else {
                     for (int b = 0; b < cnt; b += blockDim.x) {
