@@ -450,10 +450,9 @@ static __device__ __forceinline__ void publish_row(const Job& J, int s, const in
 // nothing.  Equality is decided on the full rows, never on the hash.
 template <int SS>
 static __device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int (&row)[SS],
-                               int* s_claims)
+                               int* s_claims, bool published = false)
 {
     uint32_t idx = (uint32_t)h & J.mask;
-    bool published = false;
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
         unsigned long long w = ld_acquire_u64(&J.table[idx]);
         if (w == kEmptySlot) {
@@ -801,16 +800,33 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                 if (!same && J.algo == DFAMIN_ALG_LEADER) {
                     slot = naive_elect(J, s, L);
                     moved = true;
-                } else if (!same) {                   // T(s) != T(leader): regroup
+                } else if (!same) {
+                    // T(s) != T(leader): publish the row and list s with its first probe
+                    // position; the inserts run below, packed into full warps
                     uint64_t h = hash_begin(L);
 #pragma unroll
                     for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
                     h = hash_final(h, L, J.flags);
-                    slot = insert_row<SS>(J, s, h, row, s_claims);
-                    moved = slot != kFail;
+                    store_row<SS>(J.sig, s, row);
+                    slot = (uint32_t)h & J.mask;
+                    moved = true;
                 }
             }
             append_moved(J, c0, moved, s, slot, s_cnt);
+        }
+        if (J.algo != DFAMIN_ALG_LEADER) {
+            // ---- regroup the listed states: every lane of a warp has an insert to do
+            __threadfence();                          // each thread's rows visible device-wide
+            __syncthreads();                          // ... before any lane claims a slot
+            const int cnt = *s_cnt;
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int s = __ldcg(&J.lst_s[c0 + i]);
+                const uint32_t idx = __ldcg(&J.lst_slot[c0 + i]);
+                int row[SS];
+                load_row<SS>(J.sig, s, row);
+                const uint32_t slot = insert_row<SS>(J, s, (uint64_t)idx, row, s_claims, true);
+                J.lst_slot[c0 + i] = slot;
+            }
         }
     } else {
         const int nch = (ncols + 4) / 4;
@@ -1058,14 +1074,30 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     if (threadIdx.x == 0) s_claims = 0;
                     __syncthreads();
                     int mine = 0;
-                    for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
-                        int r[KC];
-                        load_succ<KC>(J.delta, q, r);
-                        uint32_t code = (uint32_t)__ldcs(&pidx[q]);
+                    // two states per thread per step: their gathers and atomics overlap
+                    for (int q0 = c0 + threadIdx.x; q0 < c1; q0 += 2 * blockDim.x) {
+                        uint32_t code[2];
+                        int qv[2] = {q0, q0 + (int)blockDim.x};
 #pragma unroll
-                        for (int c = 0; c < KC; ++c) code = (code << PB) | (uint32_t)ld_blk(&pidx[r[c]]);
-                        J.lst_slot[q] = code;
-                        if (atomicMin(&dtab[code], (uint32_t)q) == 0xffffffffu) ++mine;
+                        for (int u = 0; u < 2; ++u) {
+                            code[u] = 0;
+                            if (qv[u] >= c1) continue;
+                            int r[KC];
+                            load_succ<KC>(J.delta, qv[u], r);
+                            code[u] = (uint32_t)__ldcs(&pidx[qv[u]]);
+#pragma unroll
+                            for (int c = 0; c < KC; ++c)
+                                code[u] = (code[u] << PB) | (uint32_t)ld_blk(&pidx[r[c]]);
+                        }
+                        uint32_t old[2] = {0u, 0u};
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            if (qv[u] >= c1) continue;
+                            J.lst_slot[qv[u]] = code[u];
+                            old[u] = atomicMin(&dtab[code[u]], (uint32_t)qv[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) mine += qv[u] < c1 && old[u] == 0xffffffffu;
                     }
                     mine = cta_sum(mine);
                     if (threadIdx.x == 0) {
@@ -1078,17 +1110,23 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     // every group's smallest state leads it and lists its table word for reset
                     if (threadIdx.x == 0) s_rst = 0;
                     __syncthreads();
-                    for (int b = c0; b < c1; b += blockDim.x) {
-                        const int q = b + (int)threadIdx.x;
-                        bool lead = false;
-                        uint32_t code = 0;
-                        if (q < c1) {
-                            code = __ldcs(&J.lst_slot[q]);
-                            const int m = (int)__ldcg(&dtab[code]);
-                            J.block[q] = m;
-                            lead = m == q;
+                    for (int b = c0; b < c1; b += 4 * (int)blockDim.x) {
+                        int qv[4], mv[4];
+                        uint32_t cv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            qv[u] = b + u * (int)blockDim.x + (int)threadIdx.x;
+                            cv[u] = qv[u] < c1 ? __ldcs(&J.lst_slot[qv[u]]) : 0u;
                         }
-                        append_pair(J, c0, &s_rst, lead, q, code >> 1);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            mv[u] = qv[u] < c1 ? (int)__ldcg(&dtab[cv[u]]) : -1;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (qv[u] < c1) J.block[qv[u]] = mv[u];
+                            append_pair(J, c0, &s_rst, qv[u] < c1 && mv[u] == qv[u], qv[u],
+                                        cv[u] >> 1);
+                        }
                     }
                     __syncthreads();
                     const int nnew = s_rst;
