@@ -74,6 +74,32 @@ def profiled_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def gather_roofline(n: int, k: int, passes: int, kernel_ms: float):
+    """The rounds are bound by random block-id gathers served from L2, not by HBM bytes.  This
+    compares the minimum gathers of the path (passes x n x k per launch) with the GPU's random
+    4-byte gather rate, measured here on a table of n ints by the probe built beside the
+    library (four gathers per element, best of 5 launches)."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2410_22764_gb300", "probe", "libgatherprobe.so")
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError as e:
+        return {"unavailable": f"gather probe not built: {e}"}
+    lib.gather_probe.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_float)]
+    lib.gather_probe.restype = ctypes.c_int
+    ms = ctypes.c_float(0.0)
+    rc = lib.gather_probe(n, n, 5, ctypes.byref(ms))
+    if rc != 0:
+        return {"unavailable": f"gather probe failed (CUDA error {rc})"}
+    ceiling = 4.0 * n / (ms.value / 1e3) / 1e9
+    gathers = float(passes) * n * k
+    achieved = gathers / (kernel_ms / 1e3) / 1e9
+    return {"bound": "l2_random_gathers", "unit": "G gathers/s", "achieved": achieved,
+            "peak": ceiling, "frac": achieved / ceiling,
+            "gathers_per_launch": gathers, "probe": f"{n} x 4 random int32 loads, table {n} ints"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -294,6 +320,7 @@ def main():
     kernel_ms = statistics.mean(step_ms)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     traffic = profiled_traffic("team_kernel", "config2")
+    gather = gather_roofline(n, k, passes, kernel_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "edge-visits/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
@@ -312,6 +339,7 @@ def main():
                      "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "team_kernel",
                      "algorithmic_bytes_per_launch": alg_bytes},
+        "gather_roofline": gather,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
