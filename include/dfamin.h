@@ -163,7 +163,8 @@ dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t *state_off, 
 /* Plan creation and destruction use stream-ordered allocation on a library stream and never
  * wait for work on other streams.  Destroying a plan releases its device table after the most
  * recent launch that used it has completed (in stream order); a caller that launches one plan
- * on several streams at once must let those launches complete before destroying it. */
+ * on several streams at once must let those launches complete before destroying it.  A launch
+ * captured into a CUDA graph is not tracked: the plan must outlive every replay of the graph. */
 dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan);
 
 /* Bytes of device workspace a launch with this plan needs (caller-owned, 256-byte aligned). */

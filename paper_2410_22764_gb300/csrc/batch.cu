@@ -174,7 +174,8 @@ struct dfamin_batch_plan_s {
     dfamin_options opt{};
     std::vector<BatchDesc> desc;   // ticket order
     BatchDesc* d_desc = nullptr;   // device copy, owned
-    cudaEvent_t last_launch = nullptr;  // recorded on the stream of every launch
+    cudaEvent_t last_launch = nullptr;  // recorded on the stream of every uncaptured launch
+    bool recorded = false;              // last_launch has been recorded at least once
     int64_t tickets = 0;
     int grid = 0;
     size_t dsmem = 0;
@@ -382,7 +383,7 @@ DFAMIN_API dfamin_status dfamin_batch_plan_destroy(dfamin_batch_plan plan)
         // that launch is still running), without blocking the host
         cudaStream_t ps = nullptr;
         if (plan_stream(plan->dev, &ps) == DFAMIN_OK) {
-            if (plan->last_launch) cudaStreamWaitEvent(ps, plan->last_launch, 0);
+            if (plan->recorded) cudaStreamWaitEvent(ps, plan->last_launch, 0);
             cudaFreeAsync(plan->d_desc, ps);
         }
     }
@@ -453,7 +454,17 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
                                              (cudaStream_t)stream),
                  "batch_kernel cooperative launch"))
         return DFAMIN_ECUDA;
-    if (!cuda_ok(cudaEventRecord(plan->last_launch, (cudaStream_t)stream), "cudaEventRecord(plan)"))
+    // outside stream capture the launch is marked so that the plan's release waits for it; a
+    // launch captured into a graph cannot be waited on from outside, and the caller keeps the
+    // plan alive while the graph may be replayed
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!cuda_ok(cudaStreamIsCapturing((cudaStream_t)stream, &cap), "cudaStreamIsCapturing"))
         return DFAMIN_ECUDA;
+    if (cap == cudaStreamCaptureStatusNone) {
+        if (!cuda_ok(cudaEventRecord(plan->last_launch, (cudaStream_t)stream),
+                     "cudaEventRecord(plan)"))
+            return DFAMIN_ECUDA;
+        plan->recorded = true;
+    }
     return DFAMIN_OK;
 }

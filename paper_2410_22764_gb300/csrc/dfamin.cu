@@ -254,6 +254,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
         int per_sm = 0;
         st = kernel_ctas_per_sm(dev, (const void*)small_kernel, kThreads, smem, &per_sm);
         if (st != DFAMIN_OK) return st;
+        (void)cudaGetLastError();   // the check below must see this launch's error only
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
         return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
     }

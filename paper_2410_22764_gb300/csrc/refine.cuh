@@ -1386,7 +1386,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
                 heads += (b.x == s) + (b.y == s + 1) + (b.z == s + 2) + (b.w == s + 3);
             } else {
-                for (int j = s; j < c1; ++j) heads += (ld_blk(&J.block[j]) == j);
+                for (int j = s; j < min(s + 4, c1); ++j) heads += (ld_blk(&J.block[j]) == j);
             }
         }
         heads = cta_sum(heads);
@@ -1431,7 +1431,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 r.w = b.w == s + 3 ? o.w : __ldcg(&J.out_block[b.w]);
                 *reinterpret_cast<int4*>(J.out_block + s) = r;
             } else {
-                for (int j = s; j < c1; ++j) {
+                for (int j = s; j < min(s + 4, c1); ++j) {
                     const int L = ld_blk(&J.block[j]);
                     if (L != j) J.out_block[j] = __ldcg(&J.out_block[L]);
                 }

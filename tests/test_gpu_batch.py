@@ -176,3 +176,30 @@ def test_plan_destroyed_right_after_launch(dm):
         for i, (b, nb, ps) in enumerate(want):
             assert p[2, i] == 0 and p[0, i] == nb and p[1, i] == ps
             assert np.array_equal(o[i], b)
+
+
+def test_single_calls_after_graph_captured_plan_is_released(dm):
+    # releasing a plan whose launch was captured into a graph must leave no pending CUDA error
+    # behind for later, unrelated calls
+    dfas = mixed_batch(12, count=10, max_n=5000)
+    delta, acc, state_off, ks = dm.pack_batch(dfas)
+    plan = dm.BatchPlan(state_off, ks, dm.options())
+    dd = torch.from_numpy(delta).cuda()
+    aa = torch.from_numpy(acc.view(np.int32)).cuda()
+    ws = dm.Workspace()
+    out = torch.empty(plan.states, dtype=torch.int32, device="cuda")
+    per = torch.zeros((3, plan.count), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.run(dd, aa, workspace=ws, out_block=out, per_dfa=per, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(dd, aa, workspace=ws, out_block=out, per_dfa=per, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    del g
+    plan.close()
+    d = I.random_dfa(1, 0, 1.0, 1)
+    got, nb, ps, st = dm.minimize_host(d.n, d.k, d.delta, d.accept)
+    assert st == 0 and nb == 1
