@@ -180,9 +180,11 @@ static __device__ __forceinline__ int ld_blk(const int32_t* p)
 {
 #if DFAMIN_GATHER_KEEP
     uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     int v;
-    asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
+    // volatile keeps the load in place relative to barriers; no memory clobber, so independent
+    // loads around it (successors, other gathers) can be issued back to back
+    asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 #else
     return __ldcg(p);
@@ -479,43 +481,40 @@ static __device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int
     return kFail;
 }
 
-// Chunk v (4 entries) of the row (head, block[succ(s,0)], ..., block[succ(s,ncols-1)], 0...).
-static __device__ __forceinline__ void row_chunk(const Job& J, int s, int head, int v, int ncols,
-                                          int (&x)[4])
+// Chunks v0 .. v0+3 (16 entries) of the row (head, block[succ(s,0)], ...), with every
+// successor load issued before the first gather, and every gather before the first use.
+static __device__ __forceinline__ void row_chunk4(const Job& J, int s, int head, int v0, int ncols,
+                                           int (&x)[16])
 {
+    int t[16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = 4 * v + j;
-        int t = 0;
-        if (i >= 1 && i <= ncols) {
-            t = succ_col(J, s, i - 1);
-            if ((unsigned)t >= (unsigned)J.n) { set_status(J.ctrl, DFAMIN_EINVAL); t = 0; }
+    for (int j = 0; j < 16; ++j) {
+        const int i = 4 * v0 + j;
+        t[j] = (i >= 1 && i <= ncols) ? succ_col(J, s, i - 1) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int i = 4 * v0 + j;
+        if (i >= 1 && i <= ncols && (unsigned)t[j] >= (unsigned)J.n) {
+            set_status(J.ctrl, DFAMIN_EINVAL);
+            t[j] = 0;
         }
-        x[j] = (i == 0) ? head : (i <= ncols ? ld_blk(&J.block[t]) : 0);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int i = 4 * v0 + j;
+        x[j] = i == 0 ? head : (i <= ncols ? ld_blk(&J.block[t[j]]) : 0);
     }
 }
 
-static __device__ void publish_row_generic(const Job& J, int s, int head, int nch, int ncols)
+// Insert s, whose row is already stored at sig[s], starting at slot idx (runtime width).
+static __device__ uint32_t insert_stored_row(const Job& J, int s, uint32_t idx, int nch,
+                                             int* s_claims)
 {
-    int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
-    for (int v = 0; v < nch; ++v) {
-        int x[4];
-        row_chunk(J, s, head, v, ncols, x);
-        __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
-    }
-    __threadfence();
-}
-
-// Runtime-width version: s's row is regathered chunk by chunk (L1/L2-hot) for comparisons.
-static __device__ uint32_t insert_row_generic(const Job& J, int s, int head, uint64_t h, int nch,
-                                       int ncols, int* s_claims)
-{
-    uint32_t idx = (uint32_t)h & J.mask;
-    bool published = false;
+    const int4* mine = reinterpret_cast<const int4*>(J.sig + (int64_t)s * J.sig_stride);
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
         unsigned long long w = ld_acquire_u64(&J.table[idx]);
         if (w == kEmptySlot) {
-            if (!published) { publish_row_generic(J, s, head, nch, ncols); published = true; }
             w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, s));
             if (w == kEmptySlot) {
                 atomicAdd(s_claims, 1);
@@ -527,10 +526,8 @@ static __device__ uint32_t insert_row_generic(const Job& J, int s, int head, uin
             reinterpret_cast<const int4*>(J.sig + (int64_t)slot_rep(w) * J.sig_stride);
         bool eq = true;
         for (int v = 0; v < nch && eq; ++v) {
-            int x[4];
-            row_chunk(J, s, head, v, ncols, x);
-            const int4 b = __ldcg(theirs + v);
-            eq = x[0] == b.x && x[1] == b.y && x[2] == b.z && x[3] == b.w;
+            const int4 a = __ldcg(mine + v), b = __ldcg(theirs + v);
+            eq = a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
         }
         if (eq) {
             if (s < slot_min(w)) atomicMin(&J.table[idx], slot_word(s, slot_rep(w)));
@@ -744,13 +741,35 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
         }
     } else {
         const int nch = (ncols + 4) / 4;
+        if ((int64_t)nlead * 4 > (int64_t)J.n) {
+            // most states lead: visit the states in order (block[s] == s marks a leader), so a
+            // warp reads consecutive entries of every closure column instead of scattered ones
+            for (int s = gid; s < J.n; s += stride) {
+                if (ld_blk(&J.block[s]) != s) continue;
+                int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
+                for (int v0 = 0; v0 < nch; v0 += 4) {
+                    int x[16];
+                    row_chunk4(J, s, s, v0, ncols, x);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (v0 + u < nch)
+                            __stcg(out + v0 + u, make_int4(x[4 * u], x[4 * u + 1], x[4 * u + 2],
+                                                           x[4 * u + 3]));
+                }
+            }
+            return;
+        }
         for (int i = gid; i < nlead; i += stride) {
             const int s = __ldcg(&J.lead[i]);
             int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
-            for (int v = 0; v < nch; ++v) {
-                int x[4];
-                row_chunk(J, s, s, v, ncols, x);
-                __stcg(out + v, make_int4(x[0], x[1], x[2], x[3]));
+            for (int v0 = 0; v0 < nch; v0 += 4) {
+                int x[16];
+                row_chunk4(J, s, s, v0, ncols, x);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (v0 + u < nch)
+                        __stcg(out + v0 + u, make_int4(x[4 * u], x[4 * u + 1], x[4 * u + 2],
+                                                       x[4 * u + 3]));
             }
         }
     }
@@ -830,6 +849,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
         }
     } else {
         const int nch = (ncols + 4) / 4;
+        const bool defer = J.algo != DFAMIN_ALG_LEADER;
         for (int base = c0; base < c1; base += blockDim.x) {
             const int s = base + threadIdx.x;
             bool moved = false;
@@ -839,19 +859,39 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                 if (L != s) {
                     const int4* lrow =
                         reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
+                    int4* mine = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
                     bool same = true;
+                    int stored = 0;                   // leading chunks of the row written
                     uint64_t h = hash_begin(L);
-                    for (int v = 0; v < nch; ++v) {
-                        int x[4];
-                        row_chunk(J, s, L, v, ncols, x);
+                    for (int v0 = 0; v0 < nch; v0 += 4) {
+                        int4 l[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int i = 4 * v + j;
+                        for (int u = 0; u < 4; ++u)
+                            if (v0 + u < nch) l[u] = __ldcg(lrow + v0 + u);
+                        int x[16];
+                        row_chunk4(J, s, L, v0, ncols, x);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int i = 4 * v0 + j;
                             if (i >= 1 && i <= ncols) h = hash_step(h, x[j]);
                         }
-                        if (same) {
-                            const int4 l = __ldcg(lrow + v);
-                            same = l.x == x[0] && l.y == x[1] && l.z == x[2] && l.w == x[3];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (v0 + u >= nch) break;
+                            const int* y = x + 4 * u;
+                            same = same && l[u].x == y[0] && l[u].y == y[1] && l[u].z == y[2] &&
+                                   l[u].w == y[3];
+                        }
+                        // a regrouping state writes its row once, so that its inserts compare
+                        // stored rows; the chunks it shares with its leader are copied
+                        if (defer && !same) {
+                            for (int v = stored; v < v0; ++v) __stcg(mine + v, __ldcg(lrow + v));
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                if (v0 + u < nch)
+                                    __stcg(mine + v0 + u, make_int4(x[4 * u], x[4 * u + 1],
+                                                                    x[4 * u + 2], x[4 * u + 3]));
+                            stored = min(v0 + 4, nch);
                         }
                     }
                     if (!same && J.algo == DFAMIN_ALG_LEADER) {
@@ -859,12 +899,23 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                         moved = true;
                     } else if (!same) {
                         h = hash_final(h, L, J.flags);
-                        slot = insert_row_generic(J, s, L, h, nch, ncols, s_claims);
-                        moved = slot != kFail;
+                        slot = (uint32_t)h & J.mask;
+                        moved = true;
                     }
                 }
             }
             append_moved(J, c0, moved, s, slot, s_cnt);
+        }
+        if (defer) {
+            // ---- regroup the listed states, packed into full warps (rows already stored)
+            __threadfence();
+            __syncthreads();
+            const int cnt = *s_cnt;
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int s = __ldcg(&J.lst_s[c0 + i]);
+                const uint32_t idx = __ldcg(&J.lst_slot[c0 + i]);
+                J.lst_slot[c0 + i] = insert_stored_row(J, s, idx, nch, s_claims);
+            }
         }
     }
 }
