@@ -5,8 +5,8 @@ The knobs change no result, only speed:
     shared-memory kernel (``smem_states``);
   * batches: the one-CTA limit (``smem_states``), the states per CTA when sizing a team
     (``team_states``) and a cap on the grid (``ctas``).
-Regrouping uses the hash table with full-row verification throughout (there is no second
-regrouping algorithm to choose from).
+With ``allow_leader=True`` a single DFA may also be given the leader election (Alg. 2 naivePR,
+``algorithm=1``): the partition is the same, the round count is that algorithm's own.
 
 Candidates are timed on the device (CUDA events, median of a few runs after warm-up) and the
 fastest is stored in a JSON cache keyed by GPU name and a shape bucket, so later calls with a
@@ -44,8 +44,9 @@ def _store(path: str, data: dict):
     os.replace(tmp, path)
 
 
-def single_key(gpu: str, n: int, k: int, closure: bool) -> str:
-    return f"{gpu}|single|n2^{round(math.log2(max(n, 1)))}|k{k}|c{int(closure)}"
+def single_key(gpu: str, n: int, k: int, closure: bool, leader: bool = False) -> str:
+    return (f"{gpu}|single|n2^{round(math.log2(max(n, 1)))}|k{k}|c{int(closure)}"
+            + ("|alg" if leader else ""))
 
 
 def batch_key(gpu: str, ns, ks, closure: bool) -> str:
@@ -56,10 +57,12 @@ def batch_key(gpu: str, ns, ks, closure: bool) -> str:
             f"|t2^{round(math.log2(max(trans, 1)))}|k{round(meank)}|c{int(closure)}")
 
 
-def single_candidates(n: int, sms: int) -> list[dict]:
+def single_candidates(n: int, sms: int, leader: bool = False) -> list[dict]:
     cands = [{"ctas": c * sms} for c in (1, 2, 3, 4)]
     if n <= 8192:
         cands += [{"smem_states": max(n, 1)}, {"smem_states": 1}]
+    if leader:
+        cands += [dict(c, algorithm=1) for c in cands if "smem_states" not in c]
     return cands
 
 
@@ -118,18 +121,23 @@ def _time_ms(fn, warmup=2, reps=3) -> float:
 
 
 def tune_single(n: int, k: int, delta, accept, closure: bool = False, retune: bool = False,
-                path: str | None = None):
+                path: str | None = None, allow_leader: bool = False):
     """Tuned options for one DFA (device tensors delta, accept)."""
     from . import dfamin
     gpu, sms = _gpu_name_and_sms()
     ws = dfamin.Workspace()
 
+    def opts(c):
+        c = dict(c)
+        leader = c.pop("algorithm", 0) == 1
+        return dfamin.options(closure=closure, leader=leader, **c)
+
     def measure(c):
-        opt = dfamin.options(closure=closure, **c)
+        opt = opts(c)
         return _time_ms(lambda: dfamin.minimize_ex(n, k, delta, accept, opt=opt, workspace=ws))
-    best, timings = choose(single_key(gpu, n, k, closure), single_candidates(n, sms), measure,
-                           path, retune)
-    return dfamin.options(closure=closure, **best), timings
+    best, timings = choose(single_key(gpu, n, k, closure, allow_leader),
+                           single_candidates(n, sms, allow_leader), measure, path, retune)
+    return opts(best), timings
 
 
 def tune_batch(state_off, ks, delta, accept, closure: bool = False, retune: bool = False,

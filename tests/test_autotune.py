@@ -59,3 +59,29 @@ def test_tuned_options_give_default_results(tmp_path):
     o2, p2 = default.run(dd, aa)
     torch.cuda.synchronize()
     assert torch.equal(o1, o2) and torch.equal(p1, p2)
+
+
+def test_leader_candidates_only_when_allowed():
+    plain = autotune.single_candidates(100000, 152)
+    both = autotune.single_candidates(100000, 152, leader=True)
+    assert not any("algorithm" in c for c in plain)
+    assert {json.dumps(c, sort_keys=True) for c in plain} < {json.dumps(c, sort_keys=True)
+                                                              for c in both}
+    assert all(c.get("algorithm") == 1 for c in both if c not in plain)
+    assert autotune.single_key("G", 10**5, 4, False, True) != autotune.single_key("G", 10**5, 4,
+                                                                                   False)
+
+
+@pytest.mark.gpu
+def test_tuner_may_pick_the_leader_election(tmp_path):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22764_gb300 import dfamin, inputs as I
+    d = I.bitsplitter_dfa(14)
+    dd, aa = dfamin.to_device(d.delta, d.accept)
+    opt, timings = autotune.tune_single(d.n, d.k, dd, aa, path=str(tmp_path / "t.json"),
+                                        allow_leader=True)
+    assert any('"algorithm": 1' in key for key in timings)
+    got = dfamin.minimize_ex(d.n, d.k, dd, aa, opt=opt).host()
+    want = dfamin.minimize_ex(d.n, d.k, dd, aa).host()
+    assert np.array_equal(got[0], want[0]) and got[1] == want[1] and got[3] == 0
