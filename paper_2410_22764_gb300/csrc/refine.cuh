@@ -1280,17 +1280,98 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             }
         }
         const int ncols = k + ncl_cols;
+        // ---- runtime-width round 1 by acceptance keys.  In P0 a signature is exactly the
+        //      acceptance of the state and of its ncols successors; with ncols < 32 that is a
+        //      32-bit key, stored in the table slot beside the group's smallest state (slot =
+        //      (min << 32) | key), so the round publishes and compares no rows.
+        bool keys_done = false;
+        int keys_count0 = count;
+        if constexpr (KC == 0) {
+            if (!round1_done && J.algo == DFAMIN_ALG_SIGNATURE && ncols < 32 && count < n) {
+                int mine = 0;
+                for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+                    uint32_t key = is_accepting(J, q) ? 1u : 0u;
+                    for (int b = 0; b < ncols; b += 16) {
+                        int t[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) t[j] = b + j < ncols ? succ_col(J, q, b + j) : 0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (b + j >= ncols) continue;
+                            if ((unsigned)t[j] >= (unsigned)n) set_status(J.ctrl, DFAMIN_EINVAL);
+                            else key |= (is_accepting(J, t[j]) ? 1u : 0u) << (b + j + 1);
+                        }
+                    }
+                    uint64_t hk = (uint64_t)key * 0x9E3779B97F4A7C15ull;
+                    hk ^= hk >> 29;
+                    uint32_t idx = (uint32_t)hk & J.mask;
+                    uint32_t probe = 0;
+                    for (; probe <= J.mask; ++probe) {
+                        unsigned long long w = ld_acquire_u64(&J.table[idx]);
+                        if (w == kEmptySlot) {
+                            w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(q, (int)key));
+                            if (w == kEmptySlot) { ++mine; break; }
+                        }
+                        if ((uint32_t)w == key) {
+                            if (q < slot_min(w)) atomicMin(&J.table[idx], slot_word(q, (int)key));
+                            break;
+                        }
+                        idx = (idx + 1) & J.mask;
+                    }
+                    if (probe > J.mask) set_status(J.ctrl, DFAMIN_EPROBE);
+                    J.lst_slot[q] = idx;
+                }
+                mine = cta_sum(mine);
+                if (threadIdx.x == 0) {
+                    if (mine) atomicAdd(&J.ctrl->claims, (unsigned long long)mine);
+                    if (rank == 0) J.ctrl->nlead = 0;    // the list is rebuilt below
+                }
+                if (!team_barrier(ts)) goto done;
+                trace_mark(J, tw, 1, 5);
+                // every group's smallest state leads it and lists its slot for reset
+                if (threadIdx.x == 0) s_rst = 0;
+                __syncthreads();
+                for (int b = c0; b < c1; b += blockDim.x) {
+                    const int q = b + (int)threadIdx.x;
+                    bool lead = false;
+                    uint32_t slot = 0;
+                    if (q < c1) {
+                        slot = __ldcs(&J.lst_slot[q]);
+                        const int m = slot_min(__ldcg(&J.table[slot]));
+                        J.block[q] = m;
+                        lead = m == q;
+                    }
+                    append_pair(J, c0, &s_rst, lead, q, slot);
+                }
+                __syncthreads();
+                const int nnew = s_rst;
+                if (threadIdx.x == 0) s_base = nnew ? atomicAdd(&J.ctrl->nlead, nnew) : 0;
+                __syncthreads();
+                for (int i = threadIdx.x; i < nnew; i += blockDim.x) {
+                    J.lead[s_base + i] = J.stg[c0 + i];
+                    J.lead_slot[s_base + i] = J.lst_rst[c0 + i];
+                }
+                if (!team_barrier(ts)) goto done;
+                trace_mark(J, tw, 1, 6);
+                count = (int)ld_acquire_u64(&J.ctrl->claims);
+                passes = 1;
+                keys_done = true;
+            }
+        }
         const int max_passes = J.max_passes;
-        unsigned long long claims_seen = round2_done ? (unsigned long long)round1_count2 : 0ull;
-        // leaders of the first rounds own no group slot, except after the dense round 2,
-        // whose every leader lists the table word it used
-        int lead_reset_from = round2_done ? 0 : ld_volatile(&J.ctrl->nlead);
+        unsigned long long claims_seen = round2_done ? (unsigned long long)round1_count2
+                                         : keys_done ? (unsigned long long)count
+                                                     : 0ull;
+        // leaders of the first rounds own no group slot, except after the dense round 2 or
+        // the key round, whose every leader lists the slot it used
+        int lead_reset_from = (round2_done || keys_done) ? 0 : ld_volatile(&J.ctrl->nlead);
         const bool leader_mode = J.algo == DFAMIN_ALG_LEADER;
         // signature rounds stop early once every block is a singleton; Alg. 2 runs until a
         // round changes nothing
         // round 1 (or 2) done above and nothing split: stable
         const bool stable1 = (round1_done && round1_count1 == round1_count0) ||
-                             (round2_done && round1_count2 == round1_count1);
+                             (round2_done && round1_count2 == round1_count1) ||
+                             (keys_done && count == keys_count0);
         while (!stable1 && (leader_mode || count < n)) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
