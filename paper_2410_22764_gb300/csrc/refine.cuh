@@ -1024,6 +1024,8 @@ static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamS
                 s_na = m;
             }
             __syncthreads();
+            // no letter changed at level i: the whole level repeats level i-1, drop it
+            if (s_na == 0) ncol -= na;
             na = s_na;
             __syncthreads();
         }
