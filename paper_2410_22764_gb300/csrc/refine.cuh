@@ -223,17 +223,20 @@ static __device__ __forceinline__ bool team_barrier(TeamSync& ts)
         int ok = 1;
         if (ld_acquire_u64(ts.bar) < target) {
             const uint64_t t0 = gtimer();
-            unsigned sleep_ns = 32;
+            // tight polling of the counter; the status word and the deadline are checked
+            // every 8th poll, and after 256 polls the waiter sleeps between polls
+            unsigned it = 0;
             for (;;) {
                 if (ld_acquire_u64(ts.bar) >= target) break;
-                if (ld_volatile(ts.status) != 0) { ok = 0; break; }
-                if ((int64_t)(gtimer() - t0) > ts.timeout_ns) {
-                    atomicCAS(ts.status, 0, (int)DFAMIN_ETIMEOUT);
-                    ok = 0;
-                    break;
+                if ((++it & 7u) == 0u) {
+                    if (ld_volatile(ts.status) != 0) { ok = 0; break; }
+                    if ((int64_t)(gtimer() - t0) > ts.timeout_ns) {
+                        atomicCAS(ts.status, 0, (int)DFAMIN_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (it > 256u) __nanosleep(128);
                 }
-                __nanosleep(sleep_ns);
-                if (sleep_ns < 256) sleep_ns <<= 1;
             }
         }
         __threadfence();
