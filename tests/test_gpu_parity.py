@@ -283,3 +283,21 @@ def test_team_kernel_tiny_and_pattern_round(dm, n, k):
         d = I.random_dfa(n, k, p, 77 * n + k)
         for ctas in (0, 3):
             check(dm, d, ctas=ctas, smem_states=1)
+
+
+@pytest.mark.parametrize("k", [9, 16, 30, 31, 32, 33])
+def test_runtime_width_key_round_boundary(dm, k):
+    # round 1 by acceptance keys needs k + 1 <= 32 bits; 31 is the last width it takes
+    for n in (3000, 40000):
+        d = I.random_dfa(n, k, 0.5, 5 * k + n)
+        check(dm, d, smem_states=1)
+    d, _ = I.inflated_dfa(2000, k, 4, 0.5, k)
+    check(dm, d, smem_states=1)
+
+
+@pytest.mark.parametrize("nbits", [5, 9, 11])
+def test_closure_key_round_on_bitsplitters(dm, nbits):
+    # B_n closure rows have k + k columns before the unchanged level is dropped
+    d = I.bitsplitter_dfa(nbits)
+    check(dm, d, closure=True, smem_states=1)
+    check_leader(dm, d, closure=True)
