@@ -91,7 +91,9 @@ typedef struct {
     int32_t max_passes;  /* cap on signature passes; 0 = n + 1 */
     uint32_t flags;      /* DFAMIN_FLAG_* */
     int32_t ctas;        /* 0 = automatic; otherwise number of CTAs for one DFA (tuning) */
-    int32_t smem_states; /* 0 = automatic; largest n solved by one CTA in shared memory */
+    int32_t smem_states; /* 0 = automatic; largest n solved by one CTA (up to 8192 states
+                            entirely in shared memory, up to 65535 with 16-bit block ids in
+                            shared memory and the group table in global memory) */
     int32_t team_states; /* batches: 0 = automatic; states per CTA when sizing a DFA's team */
     int32_t algorithm;   /* DFAMIN_ALG_SIGNATURE (default) or DFAMIN_ALG_LEADER */
     int32_t reserved;    /* must be 0 */

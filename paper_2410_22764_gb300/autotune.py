@@ -2,7 +2,8 @@
 
 The knobs change no result, only speed:
   * single DFAs: the grid of the multi-CTA kernel (``ctas``) and the size limit of the one-CTA
-    shared-memory kernel (``smem_states``);
+    kernels (``smem_states``: everything in shared memory up to 8,192 states, 16-bit ids in
+    shared memory up to 65,535);
   * batches: the one-CTA limit (``smem_states``), the states per CTA when sizing a team
     (``team_states``) and a cap on the grid (``ctas``).
 With ``allow_leader=True`` a single DFA may also be given the leader election (Alg. 2 naivePR,
@@ -59,7 +60,7 @@ def batch_key(gpu: str, ns, ks, closure: bool) -> str:
 
 def single_candidates(n: int, sms: int, leader: bool = False) -> list[dict]:
     cands = [{"ctas": c * sms} for c in (1, 2, 3, 4)]
-    if n <= 8192:
+    if n <= 65535:      # one CTA (shared memory) against the multi-CTA kernel
         cands += [{"smem_states": max(n, 1)}, {"smem_states": 1}]
     if leader:
         cands += [dict(c, algorithm=1) for c in cands if "smem_states" not in c]

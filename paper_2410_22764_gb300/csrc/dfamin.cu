@@ -28,6 +28,11 @@ __global__ void __launch_bounds__(kThreads) small_kernel(Job J, uint32_t cap)
     small_minimize(J, cap);
 }
 
+__global__ void __launch_bounds__(kMediumThreads, 1) medium_kernel(Job J)
+{
+    medium_minimize(J);
+}
+
 }  // namespace dfamin_dev
 
 // ------------------------------------------------------------------------------------------
@@ -257,6 +262,24 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
         (void)cudaGetLastError();   // the check below must see this launch's error only
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
         return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
+    }
+    // one CTA with 16-bit ids and delta in shared memory (no closure): when asked
+    // (smem_states >= n), or by default when a round's shared-memory work is small
+    // (n * (2k + 1) <= 200,000), where it beats three grid barriers per round
+    if (L.d.levels == 1 && n > (o.algorithm == DFAMIN_ALG_SIGNATURE ? kSmallMaxStates / 2 : 0) &&
+        n <= kMediumMaxStates) {
+        const bool pick = o.smem_states > 0 ? n <= o.smem_states
+                                            : (int64_t)n * (2 * (int64_t)k + 1) <= 200000;
+        const size_t msmem = align_up(sizeof(uint16_t) * (size_t)n * (size_t)(k + 1), 16);
+        int per_sm = 0;
+        if (pick && msmem + 1024 <= smem_optin &&
+            kernel_ctas_per_sm(dev, (const void*)medium_kernel, kMediumThreads, msmem, &per_sm) ==
+                DFAMIN_OK &&
+            per_sm >= 1) {
+            (void)cudaGetLastError();
+            medium_kernel<<<1, kMediumThreads, msmem, stream>>>(J);
+            return cuda_ok(cudaGetLastError(), "medium_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
+        }
     }
     size_t dsmem = 0;
     const void* kern = team_kernel_for(k, L.d.levels > 1, delta, &dsmem);

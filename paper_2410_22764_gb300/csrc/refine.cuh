@@ -1730,4 +1730,154 @@ static __device__ void small_minimize(const Job& J, uint32_t cap)
     if (threadIdx.x == 0) write_outputs(J, offset, passes);
 }
 
+// ------------------------------------------------------------------------------------------
+// Medium kernel: one CTA of kMediumThreads threads refines a DFA with n <= kMediumMaxStates
+// (no closure), by signature rounds or by the leader election of Alg. 2.  Block ids and delta live in shared memory as 16-bit values (exact, as
+// n <= 65535); the group table (64-bit slots, as in the team kernel) and the list of moved
+// states are in global memory.  Phases are separated by __syncthreads only, so a round costs
+// a few microseconds: for deep refinement (about one block split per round) this beats the
+// multi-CTA kernel, whose rounds need three grid barriers.
+// ------------------------------------------------------------------------------------------
+constexpr int kMediumThreads = 1024;
+constexpr int kMediumMaxStates = 65535;
+
+static __device__ bool m_rows_equal(const uint16_t* sb, const uint16_t* sd, int k, int s, int t)
+{
+    for (int c = 0; c < k; ++c)
+        if (sb[sd[s * k + c]] != sb[sd[t * k + c]]) return false;
+    return true;
+}
+
+static __device__ void medium_minimize(const Job& J)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = J.n, k = J.k;
+    uint16_t* sb = reinterpret_cast<uint16_t*>(smem);     // [n] leader ids
+    uint16_t* sd = sb + n;                                 // [n*k] delta
+    __shared__ int s_claims, s_cnt, s_bad;
+    int passes = 0, count = 0;
+
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    {
+        bool bad = false;
+        const int64_t total = (int64_t)n * k;
+        for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+            const int v = __ldg(&J.delta[i]);
+            if ((unsigned)v >= (unsigned)n) bad = true;
+            sd[i] = (uint16_t)v;
+        }
+        if (bad) s_bad = 1;
+    }
+    const bool leader_mode = J.algo == DFAMIN_ALG_LEADER;
+    if (leader_mode)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) J.naive_new[i] = 0x7fffffff;
+    else
+        for (uint64_t i = threadIdx.x; i <= (uint64_t)J.mask; i += blockDim.x)
+            J.table[i] = kEmptySlot;
+    int mf = 0x7fffffff, mn = 0x7fffffff;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        if (is_accepting(J, s)) mf = min(mf, s); else mn = min(mn, s);
+    }
+    mf = cta_min(mf);
+    mn = cta_min(mn);
+    if (s_bad) {
+        if (threadIdx.x == 0) { set_status(J.ctrl, DFAMIN_EINVAL); write_outputs(J, 0, 0); }
+        return;
+    }
+    for (int s = threadIdx.x; s < n; s += blockDim.x)
+        sb[s] = (uint16_t)(is_accepting(J, s) ? mf : mn);
+    count = (mf != 0x7fffffff) + (mn != 0x7fffffff);
+    __syncthreads();
+
+    // signature rounds stop once every block is a singleton; Alg. 2 runs until a round
+    // changes nothing
+    while (leader_mode || count < n) {
+        if (passes >= J.max_passes) {
+            if (threadIdx.x == 0) set_status(J.ctrl, DFAMIN_ENOCONVERGE);
+            break;
+        }
+        ++passes;
+        if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; }
+        __syncthreads();
+        // members: a state whose successors' ids differ from its leader's regroups by its full
+        // signature in the global table (slot = (min << 32) | representative; equality is
+        // decided on the rows, regathered from shared memory)
+        for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            const int L = sb[s];
+            if (L == s) continue;
+            bool same = true;
+            for (int c = 0; c < k; ++c) same = same && sb[sd[s * k + c]] == sb[sd[L * k + c]];
+            if (same) continue;
+            if (leader_mode) {
+                // Alg. 2: the states that differ from L form one new block, led by the
+                // smallest of them
+                if (atomicMin(&J.naive_new[L], s) == 0x7fffffff) atomicAdd(&s_claims, 1);
+                const int pos = atomicAdd(&s_cnt, 1);
+                J.lst_s[pos] = s;
+                J.lst_slot[pos] = (uint32_t)L;
+                continue;
+            }
+            uint64_t h = hash_begin(L);
+            for (int c = 0; c < k; ++c) h = hash_step(h, sb[sd[s * k + c]]);
+            h = hash_final(h, L, J.flags);
+            uint32_t idx = (uint32_t)h & J.mask;
+            uint32_t probe = 0;
+            for (; probe <= J.mask; ++probe) {
+                unsigned long long w = ld_acquire_u64(&J.table[idx]);
+                if (w == kEmptySlot) {
+                    w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, s));
+                    if (w == kEmptySlot) { atomicAdd(&s_claims, 1); break; }
+                }
+                const int rep = slot_rep(w);
+                if (sb[rep] == L && m_rows_equal(sb, sd, k, s, rep)) {
+                    if (s < slot_min(w)) atomicMin(&J.table[idx], slot_word(s, rep));
+                    break;
+                }
+                idx = (idx + 1) & J.mask;
+            }
+            if (probe > J.mask) { set_status(J.ctrl, DFAMIN_EPROBE); break; }
+            const int pos = atomicAdd(&s_cnt, 1);
+            J.lst_s[pos] = s;
+            J.lst_slot[pos] = idx;
+        }
+        __syncthreads();
+        const int claims = s_claims, cnt = s_cnt;
+        if (ld_volatile(&J.ctrl->status) != 0 || claims == 0) break;
+        // moves: every listed state takes its group's smallest state as id
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t slot = __ldcg(&J.lst_slot[i]);
+            sb[__ldcg(&J.lst_s[i])] =
+                (uint16_t)(leader_mode ? __ldcg(&J.naive_new[slot])
+                                       : slot_min(__ldcg(&J.table[slot])));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t slot = __ldcg(&J.lst_slot[i]);
+            if (leader_mode) J.naive_new[slot] = 0x7fffffff;
+            else J.table[slot] = kEmptySlot;
+        }
+        __syncthreads();
+        count += claims;
+    }
+    __syncthreads();
+    if (ld_volatile(&J.ctrl->status) != 0) {
+        if (threadIdx.x == 0) write_outputs(J, 0, passes);
+        return;
+    }
+    // canonical ids: ranks of the leaders in state order, then every state takes its leader's
+    int offset = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        const int head = (s < n) && (sb[s] == s);
+        int tile_total;
+        const int pre = cta_scan_flag(head, &tile_total);
+        if (head) J.stg[s] = offset + pre;
+        offset += tile_total;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < n; s += blockDim.x) J.out_block[s] = __ldcg(&J.stg[sb[s]]);
+    if (threadIdx.x == 0) write_outputs(J, offset, passes);
+}
+
 }  // namespace dfamin_dev

@@ -216,7 +216,17 @@ def test_leader_mode_against_naive_oracle(dm, maker):
 def test_leader_mode_team_sizes(dm):
     d = I.inflated_dfa(3000, 3, 4, 0.5, 11)[0]
     for ctas in (1, 3, 32):
-        check_leader(dm, d, ctas=ctas)
+        check_leader(dm, d, ctas=ctas, smem_states=1)
+    check_leader(dm, d, smem_states=65535)            # the one-CTA kernel
+
+
+@pytest.mark.parametrize("maker", ["fib", "bits", "rand", "path"])
+def test_leader_mode_one_cta_and_team_agree(dm, maker):
+    d = {"fib": lambda: I.cyclic_fib_dfa(19), "bits": lambda: I.bitsplitter_dfa(13),
+         "rand": lambda: I.random_dfa(30000, 2, 0.5, 4), "path": lambda: I.path_fib_dfa(9000)}[maker]()
+    a = check_leader(dm, d, smem_states=65535)
+    b = check_leader(dm, d, smem_states=1)
+    assert a == b
 
 
 def test_leader_mode_batch(dm):
@@ -301,3 +311,39 @@ def test_closure_key_round_on_bitsplitters(dm, nbits):
     d = I.bitsplitter_dfa(nbits)
     check(dm, d, closure=True, smem_states=1)
     check_leader(dm, d, closure=True)
+
+
+# ---------------------------------------------------------------- one-CTA medium kernel
+@pytest.mark.parametrize("n", [4097, 9000, 30001, 65535])
+@pytest.mark.parametrize("k", [1, 2, 4, 9])
+def test_medium_kernel(dm, n, k):
+    # one CTA with 16-bit ids in shared memory, forced by smem_states >= n
+    check(dm, I.random_dfa(n, k, 0.5, n + k), smem_states=65535)
+    if n <= 30001:
+        d, _ = I.inflated_dfa(n // 4, k, 4, 0.5, k, permute=True)
+        check(dm, d, smem_states=65535)
+
+
+@pytest.mark.parametrize("i", [17, 20, 22])
+def test_medium_kernel_deep_refinement(dm, i):
+    d = I.cyclic_fib_dfa(i)
+    assert d.n <= 65535
+    assert check(dm, d, smem_states=65535) == d.n - 2
+    check(dm, d, closure=True, smem_states=65535)
+    check(dm, I.path_fib_dfa(20000), smem_states=65535)
+
+
+def test_medium_kernel_errors(dm):
+    d = I.random_dfa(20000, 2, 0.5, 1)
+    bad = d.delta.copy()
+    bad[777] = d.n
+    dlt, acc = dm.to_device(bad, d.accept)
+    r = dm.minimize_ex(d.n, d.k, dlt, acc, opt=dm.options(smem_states=65535))
+    _, gn, gp, st = r.host()
+    assert st == dm.EINVAL and gn == -dm.EINVAL
+    f = I.cyclic_fib_dfa(20)
+    dlt, acc = dm.to_device(f.delta, f.accept)
+    r = dm.minimize_ex(f.n, f.k, dlt, acc, opt=dm.options(smem_states=65535, max_passes=7))
+    _, gn, gp, st = r.host()
+    assert st == dm.ENOCONVERGE and gp == 7
+    check(dm, d, smem_states=65535)
