@@ -553,6 +553,14 @@ __device__ __forceinline__ uint32_t naive_elect(const Job& J, int s, int L)
     return (uint32_t)L;
 }
 
+// Counts the leaders (block[s] == s) a warp visits: one shared atomic per warp.  In a round
+// that moves nothing these are the final blocks, so the canonical ranks need no extra count.
+static __device__ __forceinline__ void count_heads(bool head, int* s_heads)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, head);
+    if ((threadIdx.x & 31u) == 0u && m) atomicAdd(s_heads, __popc(m));
+}
+
 // Appends (s, slot) for the lanes with `moved` set: one shared atomic per warp.
 static __device__ __forceinline__ void append_moved(const Job& J, int c0, bool moved, int s,
                                              uint32_t slot, int* s_cnt)
@@ -621,7 +629,7 @@ static __device__ void cache_clear(CtaCache<SS>& C)
 
 template <int KC>
 static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s_claims, int* s_cnt,
-                                     CtaCache<RowOf<KC>::SS>& C)
+                                     CtaCache<RowOf<KC>::SS>& C, int* s_heads)
 {
     constexpr int SS = RowOf<KC>::SS;
     constexpr int kSlots = CtaCache<SS>::kSlots;
@@ -651,6 +659,7 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         uint32_t slot = 0;
         uint64_t h = 0;
         int row[SS], lr[SS];
+        count_heads(s < c1 && L == s, s_heads);
         if (s < c1 && L != s && row_ok<KC>(J, r)) {
             const int li = L & (kLeaderCache - 1);
             if (C.lkey[li] == L) {
@@ -781,7 +790,8 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
 // ---- phase B: members compare with their leader; those that differ are regrouped.
 // The loop is uniform across the CTA so that appends can be aggregated per warp.
 template <int KC>
-static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt)
+static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt,
+                              int* s_heads)
 {
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
@@ -807,6 +817,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             }
             bool moved = false;
             uint32_t slot = 0;
+            count_heads(s < c1 && L == s, s_heads);
             if (s < c1 && L != s && row_ok<KC>(J, r)) {
                 int lr[SS];
                 load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
@@ -857,8 +868,10 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             const int s = base + threadIdx.x;
             bool moved = false;
             uint32_t slot = 0;
+            int L = -1;
+            if (s < c1) L = ld_blk(&J.block[s]);
+            count_heads(s < c1 && L == s, s_heads);
             if (s < c1) {
-                const int L = ld_blk(&J.block[s]);
                 if (L != s) {
                     const int4* lrow =
                         reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
@@ -1043,6 +1056,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     __shared__ int s_cnt;
     __shared__ int s_rst;
     __shared__ int s_base;
+    __shared__ int s_heads;
+    bool heads_valid = false;                          // cta_cnt holds this CTA's leader count
     const int n = J.n, k = J.k;
     // chunks are multiples of 32 states so that every CTA's rows start 16-byte aligned
     const int chunk = ((n + T - 1) / T + 31) / 32 * 32;
@@ -1094,7 +1109,6 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             trace_mark(J, tw, 1, 5);
             for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = ld_volatile(&J.pat_rev[i]);
             __syncthreads();
-            for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) J.block[q] = n - s_pat[J.block[q]];
             int c1cnt = 0, has_f = 0, has_n = 0;
             for (int i = 0; i < NP; ++i) {
                 if (s_pat[i] > 0) {
@@ -1102,16 +1116,29 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     if (i & 1) has_f = 1; else has_n = 1;
                 }
             }
-            if (rank == 0 && threadIdx.x == 0) {
-                int m = 0;
-                for (int i = 0; i < NP; ++i)
-                    if (s_pat[i] > 0) J.lead[m++] = n - s_pat[i];
-                J.ctrl->nlead = m;
-            }
             round1_count0 = has_f + has_n;
             round1_count1 = c1cnt;
-            if (!team_barrier(ts)) goto done;
-            trace_mark(J, tw, 1, 6);
+            // round 2 by dense codes (below) needs only the patterns: then round 1's ids and
+            // leader list, which it would overwrite, are not written
+            constexpr int PB = KC + 1;
+            bool dense_next = false;
+            if constexpr (PB * PB <= 26) {
+                const uint64_t words = 2ull * ((uint64_t)J.mask + 1);
+                dense_next = round1_count1 != round1_count0 && round1_count1 < n &&
+                             J.max_passes >= 2 && (1ull << (PB * PB)) <= words;
+            }
+            if (!dense_next) {
+                for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x)
+                    J.block[q] = n - s_pat[J.block[q]];
+                if (rank == 0 && threadIdx.x == 0) {
+                    int m = 0;
+                    for (int i = 0; i < NP; ++i)
+                        if (s_pat[i] > 0) J.lead[m++] = n - s_pat[i];
+                    J.ctrl->nlead = m;
+                }
+                if (!team_barrier(ts)) goto done;
+                trace_mark(J, tw, 1, 6);
+            }
             round1_done = true;
 
             // ---- round 2 by dense codes.  After round 1 a block is a (k+1)-bit pattern, so a
@@ -1120,11 +1147,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             //      direct table (the group table's memory seen as 32-bit words, all ones = empty):
             //      one atomicMin per state gives every group its smallest state, with no hashing
             //      and no row comparison.  Same partition and pass count as the general round.
-            constexpr int PB = KC + 1;
             if constexpr (PB * PB <= 26) {
-                const uint64_t words = 2ull * ((uint64_t)J.mask + 1);
-                if (round1_count1 != round1_count0 && round1_count1 < n && J.max_passes >= 2 &&
-                    (1ull << (PB * PB)) <= words) {
+                if (dense_next) {
                     uint32_t* dtab = reinterpret_cast<uint32_t*>(J.table);
                     const int32_t* pidx = J.naive_new;
                     if (threadIdx.x == 0) s_claims = 0;
@@ -1396,7 +1420,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 phase_leaders<KC>(J, rank, T, nlead, ncols);
             }
             __syncthreads();
-            if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; }
+            if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; s_heads = 0; }
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, passes, 4);
 
@@ -1409,17 +1433,18 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 if (use_cache) {
                     cache_clear(cache);
                     __syncthreads();
-                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache);
+                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache, &s_heads);
                 } else {
-                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
+                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads);
                 }
             } else {
-                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt);
+                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads);
             }
             __syncthreads();
             {
                 const int cl = leader_mode ? s_cnt : s_claims;   // leader mode: moved states
                 if (threadIdx.x == 0 && cl) atomicAdd(&J.ctrl->claims, (unsigned long long)cl);
+                if (threadIdx.x == 0) J.cta_cnt[rank] = s_heads;
             }
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, passes, 5);
@@ -1427,7 +1452,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             const unsigned long long claims_now = ld_acquire_u64(&J.ctrl->claims);
             const int new_groups = (int)(claims_now - claims_seen);
             claims_seen = claims_now;
-            if (new_groups == 0) break;               // partition unchanged: stable
+            if (new_groups == 0) {                    // partition unchanged: stable
+                heads_valid = true;
+                break;
+            }
 
             // ---- phase C: moved states take their group's smallest state as id; that state
             //      becomes a leader and lists the group's slot to be emptied next round
@@ -1517,18 +1545,22 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
 
         // ---- canonical ids: rank of each leader among leaders, in state order.  Chunks start
         //      at multiples of 32 states, so block[] is read as int4 (4 states per thread).
-        int heads = 0;
-        for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += 4 * blockDim.x) {
-            if (s + 3 < c1) {
-                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
-                heads += (b.x == s) + (b.y == s + 1) + (b.z == s + 2) + (b.w == s + 3);
-            } else {
-                for (int j = s; j < min(s + 4, c1); ++j) heads += (ld_blk(&J.block[j]) == j);
+        //      The per-CTA leader counts come from the last round's members phase when that
+        //      round moved nothing; otherwise they are counted here.
+        if (!heads_valid) {
+            int heads = 0;
+            for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += 4 * blockDim.x) {
+                if (s + 3 < c1) {
+                    const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
+                    heads += (b.x == s) + (b.y == s + 1) + (b.z == s + 2) + (b.w == s + 3);
+                } else {
+                    for (int j = s; j < min(s + 4, c1); ++j) heads += (ld_blk(&J.block[j]) == j);
+                }
             }
+            heads = cta_sum(heads);
+            if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
+            if (!team_barrier(ts)) goto done;
         }
-        heads = cta_sum(heads);
-        if (threadIdx.x == 0) J.cta_cnt[rank] = heads;
-        if (!team_barrier(ts)) goto done;
         trace_mark(J, tw, passes, 7);
         int offset = 0;
         for (int r = threadIdx.x; r < rank; r += blockDim.x) offset += __ldcg(&J.cta_cnt[r]);
