@@ -171,10 +171,11 @@ static __device__ __forceinline__ int is_accepting(const Job& J, int s)
 }
 
 // Block-id loads.  block[] is written in the kernel (so no non-coherent loads); its random
-// gathers are the hot traffic of every round, and with DFAMIN_GATHER_KEEP they carry an L2
-// evict-last policy so that the streamed delta rows do not push block ids out of L2.
+// gathers are the hot traffic of every round.  With DFAMIN_GATHER_KEEP they carry an L2
+// evict-last policy (measured: with the 64-bit group table that is 1.6 % slower on a 10^7-state
+// DFA than plain L2 loads, so it is off by default).
 #ifndef DFAMIN_GATHER_KEEP
-#define DFAMIN_GATHER_KEEP 1
+#define DFAMIN_GATHER_KEEP 0
 #endif
 static __device__ __forceinline__ int ld_blk(const int32_t* p)
 {
