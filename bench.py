@@ -3,7 +3,7 @@
 n = 10,000,000, permuted ids, seed 1) on one GB300 per rank and print one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config2|random1k|path|batch4b|batch4a|serve|table2]
+                  [--workload config2|random1k|path|batch4b|batch4a|serve|table2|minimal]
 
 A step is one full minimization (every refinement round until the partition is stable,
 plus the canonical renumbering) of the DFA already resident in HBM.  ``value`` is edge visits
@@ -218,7 +218,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="config2",
                     choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve",
-                             "table2"])
+                             "table2", "minimal"])
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--path-variant", default="both", choices=["both", "closure", "plain"])
     ap.add_argument("--table2-rows", default="", help="comma-separated Table 2 rows (all)")

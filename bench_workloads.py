@@ -8,6 +8,9 @@
 * batch4a   the same 4,096 draws uncapped (~6.5e9 transitions): one batched launch.
 * serve     Poisson request stream through the continuous-batching server at
             0.5 / 0.8 / 0.95 of its saturated throughput: p50 / p99 latency and DFAs/s.
+* minimal   the minimal DFA of the bench workload (n = 10^7, q0 = 0): reachability, refinement
+            of the whole DFA and the quotient on one stream, against the refinement alone; and
+            the same with a second, unreachable copy of the DFA appended (n = 2*10^7).
 * table2    the paper's own families at the sizes of Table 2 (cyclic Fib with 17,711 ..
             2,178,309 states, bit-splitters B_15 .. B_26 with up to 67M states and 25 letters),
             each minimized by signature refinement (the sortPR rounds), the leader election
@@ -321,6 +324,47 @@ def run_table2(args):
           higher=False)
 
 
+def _median_ms(fn, steps, warmup, flush):
+    return statistics.median(_time_steps(fn, steps, warmup, flush))
+
+
+def run_minimal(args):
+    d = bench.make_workload(bench.BASE_M)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    rows = {}
+    for name, dfa in (("reachable", d), ("half_unreachable", None)):
+        if dfa is None:
+            # a second copy of the DFA that no word from q0 = 0 reaches
+            delta = np.concatenate([d.delta, d.delta + np.int32(d.n)])
+            acc = I.pack_bits(np.concatenate([I.unpack_bits(d.accept, d.n)] * 2))
+            dfa = I.Dfa(2 * d.n, d.k, delta, acc)
+        dd, aa = dfamin.to_device(dfa.delta, dfa.accept)
+        ws1, ws2 = dfamin.Workspace(), dfamin.Workspace()
+        res = {}
+        steps, warm = max(3, min(args.steps, 10)), max(3, args.warmup)
+        res["refinement_ms"] = _median_ms(
+            lambda: dfamin.minimize_ex(dfa.n, dfa.k, dd, aa, workspace=ws1), steps, warm, flush)
+        out = {}
+
+        def full():
+            out["r"] = dfamin.minimal_dfa(dfa.n, dfa.k, dd, aa, 0, workspace=ws2)
+        res["minimal_dfa_ms"] = _median_ms(full, steps, warm, flush)
+        res["reachability_ms"] = _median_ms(
+            lambda: dfamin.reachable(dfa.n, dfa.k, dd, aa, 0, induced=False, workspace=ws1),
+            steps, warm, flush)
+        ns, q0m, nr, passes, st = out["r"][2].cpu().tolist()
+        assert st == 0
+        res.update({"n": dfa.n, "reachable": nr, "minimal_states": ns, "passes": passes})
+        rows[name] = res
+        del dd, aa, ws1, ws2
+        torch.cuda.empty_cache()
+    main = rows["reachable"]
+    _line("minimal DFA of the inflated random DFA (n = 10^7, k = 4, q0 = 0): reachability + "
+          "refinement + quotient on one stream", 1e3 / main["minimal_dfa_ms"], "minimal DFAs/s",
+          main["minimal_dfa_ms"], max(3, min(args.steps, 10)), max(3, args.warmup),
+          {"minimal": rows})
+
+
 def run(args):
     torch.cuda.set_device(0)
     if args.workload == "random1k":
@@ -333,4 +377,6 @@ def run(args):
         run_serve(args)
     elif args.workload == "table2":
         run_table2(args)
+    elif args.workload == "minimal":
+        run_minimal(args)
     return 0

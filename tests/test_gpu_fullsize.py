@@ -91,3 +91,16 @@ def test_batch_4096(dm, kind, samples, checked):
         d = I.batch_member(delta, acc, state_off, kk, int(i))
         assert per[0, i] == outs[i].max() + 1
         assert oracle.check_stable(d.delta, d.accept, d.n, d.k, outs[i])
+
+
+def test_minimal_dfa_1e7_against_oracle(dm):
+    # the bench workload's minimal DFA from q0 = 0 (reachability + refinement + quotient)
+    d, _ = I.inflated_dfa(1_000_000, 4, 10, 0.5, 1, permute=True)
+    wd, wa, wn, wq0, wr = oracle.minimal_dfa(d.delta, d.accept, d.n, d.k, 0)
+    dd, aa = dm.to_device(d.delta, d.accept)
+    qd, qa, sc = dm.minimal_dfa(d.n, d.k, dd, aa, 0)
+    torch.cuda.synchronize()
+    ns, q0m, nr, passes, st = sc.cpu().tolist()
+    assert st == 0 and (ns, q0m, nr) == (wn, wq0, wr)
+    assert np.array_equal(qd[: wn * d.k].cpu().numpy(), wd)
+    assert np.array_equal(qa.cpu().numpy().view(np.uint32)[: wa.size], wa)
