@@ -227,8 +227,9 @@ dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int32_t *delta,
  *              holds an entry outside [0, n) (rows of unreachable states are not read), or
  *              DFAMIN_ETIMEOUT.
  *   workspace  device, 256-byte aligned, dfamin_reach_workspace_size(n) bytes.
- * Breadth-first search; a chain of L states takes about L/256 barrier-separated levels and L
- * dependent loads, so long chains are latency-bound.
+ * Breadth-first search in which a thread keeps following the states it claims (far along a
+ * chain, briefly once the frontier grows); a chain of L states takes about L/256
+ * barrier-separated levels and L dependent loads, so long chains are latency-bound.
  */
 dfamin_status dfamin_reach_workspace_size(int32_t n, size_t *bytes);
 dfamin_status dfamin_reachable(int32_t n, int32_t k, const int32_t *delta, const uint32_t *accept,

@@ -7,9 +7,11 @@
 //                    order-preserving renumbering of the reached states and, optionally, the
 //                    sub-DFA they induce.  One cooperative launch; levels meet at bounded
 //                    barriers.  A thread that claims a new state keeps exploring from it with a
-//                    small private stack (up to kReachBudget states per frontier entry) before
-//                    handing the rest to the next level, so a chain of length L takes about
-//                    L / kReachBudget levels instead of L.
+//                    small private stack before handing the rest to the next level: up to
+//                    kReachBudgetChain states per frontier entry while the frontier stays tiny
+//                    (a chain of length L then takes about L / 256 levels instead of L), up to
+//                    kReachBudgetWide once it grows (so a branching graph spreads over all
+//                    threads instead of being walked by a few).
 //   quotient_kernel  the minimal DFA from a partition: every class (restricted to reachable
 //                    states when a renumbering is given) is represented by its smallest member;
 //                    classes are numbered in the order of their representatives, and
@@ -34,7 +36,8 @@ namespace dfamin_dev {
 namespace cg = cooperative_groups;
 
 constexpr int kReachStack = 16;      // private DFS stack of a thread (entries)
-constexpr int kReachBudget = 256;    // states one frontier entry may expand within a level
+constexpr int kReachBudgetChain = 256;   // states a frontier entry may expand on a chain
+constexpr int kReachBudgetWide = 8;      // ... and on a graph whose frontier grows
 
 struct ReachCtrl {
     unsigned long long bar;          // team barrier counter
@@ -77,10 +80,10 @@ static __device__ __forceinline__ void frontier_push(int32_t* G, int* cnt, int v
 // Expands frontier entry s0: every successor not yet visited is claimed (atomicOr on the
 // bitmap); claimed states are explored by this thread while its budget lasts, the rest go to
 // the next level.  Every state enters some frontier at most once, so a frontier holds <= n.
-static __device__ void reach_expand(const ReachJob& R, int s0, int32_t* G, int* gcnt)
+static __device__ void reach_expand(const ReachJob& R, int s0, int32_t* G, int* gcnt, int budget)
 {
     int stack[kReachStack];
-    int sp = 0, budget = kReachBudget;
+    int sp = 0;
     stack[sp++] = s0;
     while (sp > 0) {
         const int s = stack[--sp];
@@ -124,14 +127,16 @@ __global__ void __launch_bounds__(kTeamThreads) reach_kernel(ReachJob R)
     // ---- breadth-first levels: level L reads frontier L%2 (size fcnt[L%3]) and appends to
     //      frontier (L+1)%2 (size fcnt[(L+1)%3]); fcnt[(L+2)%3], last read at level L-1, is
     //      cleared for level L+1
-    for (int level = 0;; ++level) {
+    for (int level = 0, prev = 1 << 30;; ++level) {
         const int size = ld_volatile(&R.ctrl->fcnt[level % 3]);
         if (size == 0) break;
+        const int budget = (size <= 4 && prev <= 4) ? kReachBudgetChain : kReachBudgetWide;
+        prev = size;
         if (gid == 0) R.ctrl->fcnt[(level + 2) % 3] = 0;
         const int32_t* F = (level & 1) ? R.f1 : R.f0;
         int32_t* G = (level & 1) ? R.f0 : R.f1;
         int* gcnt = &R.ctrl->fcnt[(level + 1) % 3];
-        for (int i = gid; i < size; i += stride) reach_expand(R, __ldcg(&F[i]), G, gcnt);
+        for (int i = gid; i < size; i += stride) reach_expand(R, __ldcg(&F[i]), G, gcnt, budget);
         if (!team_barrier(ts)) goto done;
     }
     if (ld_volatile(&R.ctrl->status) != 0) goto done;
