@@ -170,23 +170,28 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    d = make_workload(SAMPLE_M)
+    # every step minimizes the same family at a base size chosen so that W warm-up and K timed
+    # steps take about 90 s on one core (the oracle sustains ~2.4e7 edge visits/s, a step of
+    # base m visits about 160 m edges)
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    m = int(min(SAMPLE_M, max(5000, 90.0 / ((steps + warmup) * 160 / 2.4e7))))
+    d = make_workload(m)
+    for _ in range(warmup):
+        oracle.moore(d.delta, d.accept, d.n, d.k)
     times, visits = [], 0
     passes = 0
-    for _ in range(max(1, args.steps)):
+    for _ in range(steps):
         t0 = time.perf_counter()
         _, nb, passes = oracle.moore(d.delta, d.accept, d.n, d.k)
         times.append(time.perf_counter() - t0)
         visits += d.n * d.k * passes
-        if sum(times) > 60:
-            break
     total = sum(times)
     value = visits / total
-    sample = (f"inflated random DFA base m={SAMPLE_M} k={K} c={C} (n={d.n}), seed {SEED}, "
-              f"{len(times)} run(s), {passes} passes each")
+    sample = (f"inflated random DFA base m={m} k={K} c={C} (n={d.n}), seed {SEED}, "
+              f"{len(times)} timed run(s) after {warmup} warm-up run(s), {passes} passes each")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edge-visits/s",
-        "n_gpus": world, "steps": len(times), "warmup": 0,
+        "n_gpus": world, "steps": len(times), "warmup": warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
