@@ -176,11 +176,35 @@ dfamin_status dfamin_batch_workspace_size(dfamin_batch_plan plan, size_t *bytes)
 dfamin_status dfamin_batch_plan_info(dfamin_batch_plan plan, int32_t *grid, int64_t *tickets,
                                      int64_t *states, int64_t *transitions);
 
-/* Enqueue the minimization of every DFA of the plan's batch on `stream`; asynchronous. */
-dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int32_t *delta,
+/* Enqueue the minimization of every DFA of the plan's batch on `stream`; asynchronous.
+ *   delta     concatenated int32 rows, successor ids LOCAL to each DFA (DFA i's rows start at
+ *             sum_{j<i} n_j*k_j); accept one bitmap, bit state_off[i] + s for state s of DFA i.
+ *   out_block concatenated [state_off[count]], canonical ids local to each DFA.
+ *   nblocks, passes, status  device int32 [count] (passes and status may be NULL); a DFA with a
+ *             device error gets status != 0 and nblocks = -status, the others are unaffected. */
+dfamin_status dfamin_batch_plan_run(dfamin_batch_plan plan, const int32_t *delta,
                                     const uint32_t *accept, int32_t *out_block, int32_t *nblocks,
                                     int32_t *passes, int32_t *status, void *workspace,
                                     size_t workspace_bytes, dfamin_stream_t stream);
+
+/*
+ * dfamin_minimize_batch - one-shot form of the batch (no plan object): the schedule is computed
+ * on the host for this call and its descriptor table is copied into the head of the caller's
+ * workspace (a copy from pageable memory: the call returns once it is staged), so the call
+ * allocates nothing.  state_off [num_dfas+1], k [num_dfas] and delta_off [num_dfas+1] (the
+ * prefix of n_i*k_i, may be NULL as it is implied) are HOST arrays, because the schedule needs
+ * the sizes; every other array is a device array with the layout of dfamin_batch_plan_run.
+ * Launches that repeat one batch shape should use a plan (scheduled once, graph-capturable).
+ */
+dfamin_status dfamin_minimize_batch_workspace_size(int32_t num_dfas, const int64_t *state_off,
+                                                   const int32_t *k, const dfamin_options *opt,
+                                                   size_t *bytes);
+dfamin_status dfamin_minimize_batch(int32_t num_dfas, const int64_t *state_off, const int32_t *k,
+                                    const int64_t *delta_off, const int32_t *delta,
+                                    const uint32_t *accept, int32_t *out_block, int32_t *nblocks,
+                                    const dfamin_options *opt, void *workspace,
+                                    size_t workspace_bytes, int32_t *status,
+                                    dfamin_stream_t stream);
 
 /*
  * dfamin_minimize_static - the same minimization as dfamin_minimize_ex, for callers that cannot

@@ -225,12 +225,13 @@ size_t cache_bytes_for(int k, bool closure)
 
 }  // namespace
 
-DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* state_off,
-                                                  const int32_t* k, const dfamin_options* opt,
-                                                  dfamin_batch_plan* plan_out)
+namespace {
+
+// The host schedule of a batch: ticket order, team sizes, workspace layout, descriptors.
+dfamin_status build_schedule(int32_t count, const int64_t* state_off, const int32_t* k,
+                             const dfamin_options* opt, dfamin_batch_plan_s* P)
 {
-    if (!plan_out || count < 1 || !state_off || !k) return DFAMIN_EINVAL;
-    *plan_out = nullptr;
+    if (count < 1 || !state_off || !k) return DFAMIN_EINVAL;
     dfamin_options o;
     dfamin_default_options(&o);
     if (opt) o = *opt;
@@ -270,7 +271,6 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
     if (o.ctas > 0) grid_max = std::min(grid_max, o.ctas);
     if (grid_max < 1) return DFAMIN_ECUDA;
 
-    auto* P = new dfamin_batch_plan_s;
     P->dev = dev;
     P->count = count;
     P->opt = o;
@@ -345,6 +345,24 @@ DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* 
     P->tickets = team_sum;
     P->grid = (int)std::min<int64_t>(grid_max, team_sum);
 
+    return DFAMIN_OK;
+}
+
+}  // namespace
+
+DFAMIN_API dfamin_status dfamin_batch_plan_create(int32_t count, const int64_t* state_off,
+                                                  const int32_t* k, const dfamin_options* opt,
+                                                  dfamin_batch_plan* plan_out)
+{
+    if (!plan_out) return DFAMIN_EINVAL;
+    *plan_out = nullptr;
+    auto* P = new dfamin_batch_plan_s;
+    dfamin_status st = build_schedule(count, state_off, k, opt, P);
+    if (st != DFAMIN_OK) {
+        delete P;
+        return st;
+    }
+    const int dev = P->dev;
     cudaStream_t ps = nullptr;
     st = plan_stream(dev, &ps);
     if (st != DFAMIN_OK) {
@@ -411,29 +429,20 @@ DFAMIN_API dfamin_status dfamin_batch_plan_info(dfamin_batch_plan plan, int32_t*
     return DFAMIN_OK;
 }
 
-DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int32_t* delta,
-                                               const uint32_t* accept, int32_t* out_block,
-                                               int32_t* nblocks, int32_t* passes,
-                                               int32_t* status, void* workspace,
-                                               size_t workspace_bytes, dfamin_stream_t stream)
+namespace {
+
+// One launch of a scheduled batch: descriptors at d_desc (device), workspace at base.
+dfamin_status launch_batch(const dfamin_batch_plan_s& P, const BatchDesc* d_desc,
+                           unsigned char* base, const int32_t* delta, const uint32_t* accept,
+                           int32_t* out_block, int32_t* nblocks, int32_t* passes,
+                           int32_t* status, cudaStream_t stream)
 {
-    if (!plan || !accept || !out_block || !nblocks || !workspace) return DFAMIN_EINVAL;
-    if (plan->total_delta > 0 && !delta) return DFAMIN_EINVAL;
-    if (((uintptr_t)workspace & 255u) != 0 || ((uintptr_t)delta & 3u) != 0 ||
-        ((uintptr_t)accept & 3u) != 0)
-        return DFAMIN_EINVAL;
-    if (workspace_bytes < plan->ws_bytes) return DFAMIN_ENOMEM;
-    int dev = 0;
-    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
-    if (dev != plan->dev) return DFAMIN_EINVAL;
-    unsigned char* base = (unsigned char*)workspace;
-    if (!cuda_ok(cudaMemsetAsync(base, 0, plan->zero_end, (cudaStream_t)stream),
-                 "cudaMemsetAsync(batch control)"))
+    if (!cuda_ok(cudaMemsetAsync(base, 0, P.zero_end, stream), "cudaMemsetAsync(batch control)"))
         return DFAMIN_ECUDA;
     BatchArgs A{};
-    A.desc = plan->d_desc;
-    A.count = plan->count;
-    A.tickets = plan->tickets;
+    A.desc = d_desc;
+    A.count = P.count;
+    A.tickets = P.tickets;
     A.delta = delta;
     A.accept = accept;
     A.out_block = out_block;
@@ -442,18 +451,50 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
     A.status = status;
     A.ws = base;
     A.ticket = (unsigned long long*)base;
-    A.ctrl = (Ctrl*)(base + plan->off_ctrl);
-    A.nonid = (int32_t*)(base + plan->off_nonid);
-    A.pat = (int32_t*)(base + plan->off_pat);
-    A.cta_cnt = (int32_t*)(base + plan->off_cta);
-    A.flags = plan->opt.flags & ~DFAMIN_FLAG_TRACE;
-    A.algo = plan->opt.algorithm;
+    A.ctrl = (Ctrl*)(base + P.off_ctrl);
+    A.nonid = (int32_t*)(base + P.off_nonid);
+    A.pat = (int32_t*)(base + P.off_pat);
+    A.cta_cnt = (int32_t*)(base + P.off_cta);
+    A.flags = P.opt.flags & ~DFAMIN_FLAG_TRACE;
+    A.algo = P.opt.algorithm;
     void* args[] = {&A};
-    if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(plan->grid),
-                                             dim3(kTeamThreads), args, plan->dsmem,
-                                             (cudaStream_t)stream),
+    if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(P.grid),
+                                             dim3(kTeamThreads), args, P.dsmem, stream),
                  "batch_kernel cooperative launch"))
         return DFAMIN_ECUDA;
+    return DFAMIN_OK;
+}
+
+dfamin_status check_batch_args(const dfamin_batch_plan_s& P, const int32_t* delta,
+                               const uint32_t* accept, int32_t* out_block, int32_t* nblocks,
+                               void* workspace)
+{
+    if (!accept || !out_block || !nblocks || !workspace) return DFAMIN_EINVAL;
+    if (P.total_delta > 0 && !delta) return DFAMIN_EINVAL;
+    if (((uintptr_t)workspace & 255u) != 0 || ((uintptr_t)delta & 3u) != 0 ||
+        ((uintptr_t)accept & 3u) != 0)
+        return DFAMIN_EINVAL;
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return DFAMIN_ECUDA;
+    if (dev != P.dev) return DFAMIN_EINVAL;
+    return DFAMIN_OK;
+}
+
+}  // namespace
+
+DFAMIN_API dfamin_status dfamin_batch_plan_run(dfamin_batch_plan plan, const int32_t* delta,
+                                               const uint32_t* accept, int32_t* out_block,
+                                               int32_t* nblocks, int32_t* passes,
+                                               int32_t* status, void* workspace,
+                                               size_t workspace_bytes, dfamin_stream_t stream)
+{
+    if (!plan) return DFAMIN_EINVAL;
+    dfamin_status st = check_batch_args(*plan, delta, accept, out_block, nblocks, workspace);
+    if (st != DFAMIN_OK) return st;
+    if (workspace_bytes < plan->ws_bytes) return DFAMIN_ENOMEM;
+    st = launch_batch(*plan, plan->d_desc, (unsigned char*)workspace, delta, accept, out_block,
+                      nblocks, passes, status, (cudaStream_t)stream);
+    if (st != DFAMIN_OK) return st;
     // outside stream capture the launch is marked so that the plan's release waits for it; a
     // launch captured into a graph cannot be waited on from outside, and the caller keeps the
     // plan alive while the graph may be replayed
@@ -467,4 +508,68 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(dfamin_batch_plan plan, const int
         plan->recorded = true;
     }
     return DFAMIN_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// One-shot batch: the schedule is computed on the host for this call and its descriptor table
+// is copied into the head of the caller's workspace, so nothing is allocated.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+dfamin_status one_shot_layout(int32_t num_dfas, const int64_t* state_off, const int32_t* k,
+                              const int64_t* delta_off, const dfamin_options* opt,
+                              dfamin_batch_plan_s* P, size_t* desc_bytes)
+{
+    dfamin_status st = build_schedule(num_dfas, state_off, k, opt, P);
+    if (st != DFAMIN_OK) return st;
+    if (delta_off) {
+        if (delta_off[0] != 0) return DFAMIN_EINVAL;
+        for (int32_t i = 0; i < num_dfas; ++i)
+            if (delta_off[i + 1] - delta_off[i] != (state_off[i + 1] - state_off[i]) * (int64_t)k[i])
+                return DFAMIN_EINVAL;
+    }
+    *desc_bytes = align_up(sizeof(BatchDesc) * (size_t)num_dfas, 256);
+    return DFAMIN_OK;
+}
+
+}  // namespace
+
+DFAMIN_API dfamin_status dfamin_minimize_batch_workspace_size(int32_t num_dfas,
+                                                              const int64_t* state_off,
+                                                              const int32_t* k,
+                                                              const dfamin_options* opt,
+                                                              size_t* bytes)
+{
+    if (!bytes) return DFAMIN_EINVAL;
+    dfamin_batch_plan_s P;
+    size_t desc_bytes = 0;
+    const dfamin_status st = one_shot_layout(num_dfas, state_off, k, nullptr, opt, &P, &desc_bytes);
+    if (st != DFAMIN_OK) return st;
+    *bytes = desc_bytes + P.ws_bytes;
+    return DFAMIN_OK;
+}
+
+DFAMIN_API dfamin_status dfamin_minimize_batch(int32_t num_dfas, const int64_t* state_off,
+                                               const int32_t* k, const int64_t* delta_off,
+                                               const int32_t* delta, const uint32_t* accept,
+                                               int32_t* out_block, int32_t* nblocks,
+                                               const dfamin_options* opt, void* workspace,
+                                               size_t workspace_bytes, int32_t* status,
+                                               dfamin_stream_t stream)
+{
+    dfamin_batch_plan_s P;
+    size_t desc_bytes = 0;
+    dfamin_status st = one_shot_layout(num_dfas, state_off, k, delta_off, opt, &P, &desc_bytes);
+    if (st != DFAMIN_OK) return st;
+    st = check_batch_args(P, delta, accept, out_block, nblocks, workspace);
+    if (st != DFAMIN_OK) return st;
+    if (workspace_bytes < desc_bytes + P.ws_bytes) return DFAMIN_ENOMEM;
+    unsigned char* base = (unsigned char*)workspace;
+    // pageable source: the call returns once the table is staged, so the host vector may go
+    if (!cuda_ok(cudaMemcpyAsync(base, P.desc.data(), sizeof(BatchDesc) * (size_t)num_dfas,
+                                 cudaMemcpyHostToDevice, (cudaStream_t)stream),
+                 "cudaMemcpyAsync(batch table)"))
+        return DFAMIN_ECUDA;
+    return launch_batch(P, reinterpret_cast<const BatchDesc*>(base), base + desc_bytes, delta,
+                        accept, out_block, nblocks, nullptr, status, (cudaStream_t)stream);
 }

@@ -41,7 +41,9 @@ ABI_FUNCTIONS = (
     "dfamin_batch_plan_destroy",
     "dfamin_batch_workspace_size",
     "dfamin_batch_plan_info",
+    "dfamin_batch_plan_run",
     "dfamin_minimize_batch",
+    "dfamin_minimize_batch_workspace_size",
     "dfamin_reach_workspace_size",
     "dfamin_reachable",
     "dfamin_quotient_workspace_size",
@@ -90,10 +92,15 @@ def _load():
     lib.dfamin_batch_plan_destroy.argtypes = [p]
     lib.dfamin_batch_workspace_size.argtypes = [p, ctypes.POINTER(sz)]
     lib.dfamin_batch_plan_info.argtypes = [p, p, p, p, p]
-    lib.dfamin_minimize_batch.argtypes = [p, p, p, p, p, p, p, p, sz, p]
+    lib.dfamin_batch_plan_run.argtypes = [p, p, p, p, p, p, p, p, sz, p]
+    lib.dfamin_minimize_batch.argtypes = [i32, p, p, p, p, p, p, p, ctypes.POINTER(Options), p,
+                                          sz, p, p]
+    lib.dfamin_minimize_batch_workspace_size.argtypes = [i32, p, p, ctypes.POINTER(Options),
+                                                         ctypes.POINTER(sz)]
     for f in (lib.dfamin_batch_plan_create, lib.dfamin_batch_plan_destroy,
               lib.dfamin_batch_workspace_size, lib.dfamin_batch_plan_info,
-              lib.dfamin_minimize_batch):
+              lib.dfamin_batch_plan_run, lib.dfamin_minimize_batch,
+              lib.dfamin_minimize_batch_workspace_size):
         f.restype = ctypes.c_int
     lib.dfamin_reach_workspace_size.argtypes = [i32, ctypes.POINTER(sz)]
     lib.dfamin_reachable.argtypes = [i32, i32, p, p, i32, p, p, p, p, p, p, sz, p]
@@ -426,7 +433,7 @@ class BatchPlan:
     def run(self, delta: torch.Tensor, accept: torch.Tensor, *, workspace: Workspace | None = None,
             out_block: torch.Tensor | None = None, per_dfa: torch.Tensor | None = None,
             stream=None):
-        """Enqueue dfamin_minimize_batch.  Returns (out_block [states], per_dfa [3, count]
+        """Enqueue dfamin_batch_plan_run.  Returns (out_block [states], per_dfa [3, count]
         = nblocks, passes, status) as device tensors."""
         dev = accept.device
         ws = (workspace or Workspace(dev)).get(self.workspace_bytes)
@@ -434,14 +441,44 @@ class BatchPlan:
             out_block = torch.empty(self.states, dtype=torch.int32, device=dev)
         if per_dfa is None:
             per_dfa = torch.zeros((3, self.count), dtype=torch.int32, device=dev)
-        rc = _lib.dfamin_minimize_batch(
+        rc = _lib.dfamin_batch_plan_run(
             self._plan, _ptr(delta) if self.transitions > 0 else ctypes.c_void_p(0),
             _ptr(accept), _ptr(out_block), _ptr(per_dfa[0]), _ptr(per_dfa[1]),
             _ptr(per_dfa[2]), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream_handle(stream))
         if rc:
-            raise DfaminError(rc, "dfamin_minimize_batch")
+            raise DfaminError(rc, "dfamin_batch_plan_run")
         return out_block, per_dfa
 
     def split(self, out_block: np.ndarray):
         """Per-DFA views of a concatenated host out_block."""
         return [out_block[self.state_off[i]: self.state_off[i + 1]] for i in range(self.count)]
+
+
+def minimize_batch(state_off, k, delta: torch.Tensor, accept: torch.Tensor, *,
+                   opt: Options | None = None, workspace: Workspace | None = None, stream=None):
+    """Enqueue the one-shot dfamin_minimize_batch (host state_off / k, device delta / accept).
+    Returns (out_block [states], nblocks [count], status [count]) as device tensors."""
+    opt = opt or options()
+    state_off = np.ascontiguousarray(state_off, dtype=np.int64)
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    count = int(k.size)
+    pp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    need = ctypes.c_size_t(0)
+    rc = _lib.dfamin_minimize_batch_workspace_size(count, pp(state_off), pp(k), ctypes.byref(opt),
+                                                   ctypes.byref(need))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize_batch_workspace_size")
+    dev = accept.device
+    ws = (workspace or Workspace(dev)).get(need.value)
+    out_block = torch.empty(int(state_off[-1]), dtype=torch.int32, device=dev)
+    nblocks = torch.zeros(count, dtype=torch.int32, device=dev)
+    status = torch.zeros(count, dtype=torch.int32, device=dev)
+    total = int(np.sum(np.diff(state_off) * k.astype(np.int64)))
+    rc = _lib.dfamin_minimize_batch(count, pp(state_off), pp(k), ctypes.c_void_p(0),
+                                    _ptr(delta) if total > 0 else ctypes.c_void_p(0),
+                                    _ptr(accept), _ptr(out_block), _ptr(nblocks),
+                                    ctypes.byref(opt), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                                    _ptr(status), _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize_batch")
+    return out_block, nblocks, status

@@ -2,7 +2,7 @@
 
 Requests (host DFAs) arrive at any time.  The scheduler admits them in arrival order while the
 device memory they need fits in an HBM budget, packs everything admitted since the last launch
-into one batch (one persistent launch, ``dfamin_minimize_batch``) on a free stream, and keeps
+into one batch (one persistent launch, ``dfamin_batch_plan_run``) on a free stream, and keeps
 several batches in flight at once, so work of requests that arrived while others were running
 overlaps on the device.  Finished batches are found by polling their events; their results are
 copied back asynchronously and their memory returns to the budget.

@@ -1,4 +1,5 @@
-"""Batched minimization (dfamin_minimize_batch) against the oracle, DFA by DFA, bit-exact.
+"""Batched minimization (dfamin_batch_plan_run, dfamin_minimize_batch) against the oracle,
+DFA by DFA, bit-exact.
 
 Every DFA of a batch must get exactly what the oracle (and the single-DFA entry point) gives:
 canonical block ids, the block count and the pass count.
@@ -203,3 +204,19 @@ def test_single_calls_after_graph_captured_plan_is_released(dm):
     d = I.random_dfa(1, 0, 1.0, 1)
     got, nb, ps, st = dm.minimize_host(d.n, d.k, d.delta, d.accept)
     assert st == 0 and nb == 1
+
+
+@pytest.mark.parametrize("closure", [False, True])
+def test_one_shot_batch_call(dm, closure):
+    # dfamin_minimize_batch: no plan object, host offsets, table in the caller's workspace
+    dfas = mixed_batch(13, count=40, max_n=20000 if not closure else 5000)
+    want = oracle_results(dfas, closure)
+    delta, acc, state_off, ks = dm.pack_batch(dfas)
+    dd = torch.from_numpy(delta).cuda()
+    aa = torch.from_numpy(acc.view(np.int32)).cuda()
+    out, nb, st = dm.minimize_batch(state_off, ks, dd, aa, opt=dm.options(closure=closure))
+    torch.cuda.synchronize()
+    o = np.split(out.cpu().numpy(), state_off[1:-1])
+    nb, st = nb.cpu().numpy(), st.cpu().numpy()
+    for i, (b, n_b, _) in enumerate(want):
+        assert st[i] == 0 and nb[i] == n_b and np.array_equal(o[i], b)
