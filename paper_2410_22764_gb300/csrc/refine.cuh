@@ -850,6 +850,10 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
         }
         if (J.algo != DFAMIN_ALG_LEADER) {
             // ---- regroup the listed states: every lane of a warp has an insert to do
+            // Ordering: every writer fences its own row stores (they are performed in L2, the
+            // point of coherence) before the CTA barrier, and a slot is claimed only after the
+            // barrier; a reader that sees the claim (ld.acquire) reads the row from L2 (ld.cg),
+            // so it never sees an older row.
             __threadfence();                          // each thread's rows visible device-wide
             __syncthreads();                          // ... before any lane claims a slot
             const int cnt = *s_cnt;
