@@ -476,3 +476,17 @@ def test_minimal_dfa_language_and_minimality(seed):
     qd2, qa2, nb2, q0m2, nr2 = oracle.minimal_dfa(pd.reshape(-1), pacc, n2, d.k, int(perm[q0]))
     assert (nb2, nr2) == (nb, nr)
     assert _bfs_canonical(qd, qa, nb, d.k, q0m) == _bfs_canonical(qd2, qa2, nb2, d.k, q0m2)
+
+
+def test_table1_trans_iterations_are_log_of_distinguishing_depth():
+    # Alg. 1 (trans) doubles the length of the words it has examined every iteration, so its
+    # iteration count on cyclic Fib is ceil(log2 D) for the deepest distinguishing word D; the
+    # table-filling oracle measures D round by round (D = N - 2 on cyclic Fib)
+    import math
+    for name, N, iters in _read_golden("table1_rows.txt"):
+        i = int(name[3:])
+        d = I.cyclic_fib_dfa(i + 1)
+        assert d.n == int(N)
+        _, nb, rounds = oracle.tablefill(d.delta, d.accept, d.n, d.k)
+        assert nb == d.n and rounds == d.n - 2
+        assert math.ceil(math.log2(rounds)) == int(iters)
