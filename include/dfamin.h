@@ -4,8 +4,9 @@
  * Computes the coarsest partition of the states of a complete DFA that refines {F, Q\F} and is
  * stable under the transition function, i.e. language equivalence of states (arXiv 2410.22764,
  * Sec. 2 problem statement and Definition of a DFA).  The initial state is not an input and
- * unreachable states are not removed: every state is classified (Sec. 2, "we assume that all
- * the states in a DFA are reachable").  The method is signature-based partition refinement
+ * unreachable states are not removed: every state is classified (Sec. 2: the refinement
+ * algorithms take every state to be reachable; removing unreachable states is a separate
+ * pre-processing step, see dfamin_reachable).  The method is signature-based partition refinement
  * (Alg. sortPR, Sec. 3.3), optionally on the partial transitive closure A' of Alg. transPR
  * (Sec. 3.4), which has the same state equivalence as A.
  *
@@ -303,7 +304,7 @@ dfamin_status dfamin_minimal_dfa(int32_t n, int32_t k, const int32_t *delta,
                                  void *workspace, size_t workspace_bytes, dfamin_stream_t stream);
 
 /*
- * dfamin_lts_determinize - LTS -> DFA front end (Sec. 4.1, "VLTSs"): the powerset construction
+ * dfamin_lts_determinize - LTS -> DFA front end (Sec. 4.1, VLTS paragraph): the powerset construction
  * from s0 makes the LTS deterministic; every subset state accepts; one extra non-accepting state
  * (bottom) receives every missing transition and loops on every label.  HOST code on HOST
  * arrays (it prepares input for the device calls; it runs on the calling thread and uses no

@@ -623,7 +623,7 @@ int oracle_reachable(int32_t n, int32_t k, const int32_t *delta, int32_t q0, int
 }
 
 /*
- * Quotient automaton A/~ (Sec. 2, "combining undistinguishable states"): given a partition
+ * Quotient automaton A/~ (Sec. 2: merging equivalent states into one): given a partition
  * `block` of the states into nblocks classes, each stable under delta and refining {F, Q\F},
  * the class B goes to class block[delta(s, a)] on letter a for any s in B (stability makes the
  * choice irrelevant; the smallest state of B is used), B accepts iff its states do, and the
