@@ -490,3 +490,19 @@ def test_table1_trans_iterations_are_log_of_distinguishing_depth():
         _, nb, rounds = oracle.tablefill(d.delta, d.accept, d.n, d.k)
         assert nb == d.n and rounds == d.n - 2
         assert math.ceil(math.log2(rounds)) == int(iters)
+
+
+def test_bench_table2_context_matches_golden_rows():
+    # the benchmark's copy of Table 2 (sizes and alphabets) agrees with the transcribed rows
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench_workloads
+    rows = {r[0]: r for r in _read_golden("table2_rows.txt")}
+    checked = 0
+    for name, (N, k, *_times) in bench_workloads.TABLE2.items():
+        if name in rows:
+            assert int(rows[name][1]) == N and int(rows[name][2]) == k
+            checked += 1
+    assert checked >= 10
