@@ -89,7 +89,7 @@ def gather_roofline(n: int, k: int, passes: int, kernel_ms: float):
     4-byte gather rate, measured here on a table of n ints by the probe built beside the
     library (four gathers per element, best of 5 launches)."""
     import ctypes
-    path = os.path.join(ROOT, "paper_2410_22764_gb300", "probe", "libgatherprobe.so")
+    path = os.path.join(ROOT, "_build", "libgatherprobe.so")
     try:
         lib = ctypes.CDLL(path)
     except OSError as e:

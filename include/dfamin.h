@@ -78,6 +78,17 @@ typedef enum {
                                          that the full-tuple check must resolve) */
 #define DFAMIN_FLAG_HASH_CONSTANT 4u   /* testing: constant hash (every group collides) */
 #define DFAMIN_FLAG_TRACE 8u           /* record per-phase device timestamps (see below) */
+#define DFAMIN_FLAG_FULL_ROUNDS 16u    /* testing and measurement: every signature round re-reads
+                                         every state's successors.  By default a round that
+                                         follows a signature round in which few states moved is
+                                         incremental: it skips the blocks that cannot split (a
+                                         block whose members' successors all lie in blocks that
+                                         did not split in the previous round keeps its members;
+                                         same partition, same pass count) */
+#define DFAMIN_FLAG_INCREMENTAL_ROUNDS 32u /* testing: every signature round that follows another
+                                         one is incremental, however many states moved (the
+                                         default chooses by that number).  FULL_ROUNDS wins if
+                                         both are set */
 
 /* Phase trace.  With DFAMIN_FLAG_TRACE the workspace grows by DFAMIN_TRACE_BYTES, and the last
  * DFAMIN_TRACE_BYTES of the required workspace receive int64 values: [0] = number of records,
@@ -97,7 +108,13 @@ typedef struct {
                             shared memory and the group table in global memory) */
     int32_t team_states; /* batches: 0 = automatic; states per CTA when sizing a DFA's team */
     int32_t algorithm;   /* DFAMIN_ALG_SIGNATURE (default) or DFAMIN_ALG_LEADER */
-    int32_t reserved;    /* must be 0 */
+    int32_t barrier_timeout_us; /* 0 = default bound on every wait of a CTA for the other CTAs
+                            of its team (4 s for one DFA, 30 s in batches); otherwise that bound
+                            in microseconds.  A wait that runs out ends the call with status
+                            DFAMIN_ETIMEOUT (every CTA leaves at its next barrier; the context
+                            stays usable).  Meant for tests of that failure path: a bound of a
+                            few microseconds makes a multi-CTA call fail without any fault.
+                            One-CTA calls (small DFAs) have no such wait */
 } dfamin_options;
 
 /* Fills *opt with the defaults (closure off, automatic tuning). */
@@ -196,6 +213,9 @@ dfamin_status dfamin_batch_plan_run(dfamin_batch_plan plan, const int32_t *delta
  * prefix of n_i*k_i, may be NULL as it is implied) are HOST arrays, because the schedule needs
  * the sizes; every other array is a device array with the layout of dfamin_batch_plan_run.
  * Launches that repeat one batch shape should use a plan (scheduled once, graph-capturable).
+ * This one-shot call cannot be captured into a CUDA graph (its table copy reads host memory that
+ * is gone once the call returns): on a capturing stream it returns DFAMIN_EINVAL and enqueues
+ * nothing.
  */
 dfamin_status dfamin_minimize_batch_workspace_size(int32_t num_dfas, const int64_t *state_off,
                                                    const int32_t *k, const dfamin_options *opt,

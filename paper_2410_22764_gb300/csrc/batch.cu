@@ -17,6 +17,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -49,7 +50,7 @@ struct BatchDesc {             // one DFA, in ticket order
     int32_t nonid_base;        // first entry of its identity-letter flags
     int32_t pat_base;          // first entry of its round-1 pattern minima, -1 = none
     int64_t o_block, o_lst_s, o_lst_slot, o_lst_rst, o_lead, o_lead_slot, o_stg, o_table, o_sig,
-        o_cl, o_cl_letter, o_naive;
+        o_cl, o_cl_letter, o_naive, o_spl, o_cln;
 };
 
 struct BatchArgs {
@@ -70,6 +71,7 @@ struct BatchArgs {
     int32_t* cta_cnt;
     uint32_t flags;
     int32_t algo;
+    int64_t timeout_ns;            // bound on every team barrier wait
 };
 
 __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
@@ -98,6 +100,8 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.lead_slot = (uint32_t*)(r + D.o_lead_slot);
     J.stg = (int32_t*)(r + D.o_stg);
     J.naive_new = (int32_t*)(r + D.o_naive);
+    J.spl = (int32_t*)(r + D.o_spl);
+    J.cln = (int32_t*)(r + D.o_cln);
     J.algo = A.algo;
     J.table = (unsigned long long*)(r + D.o_table);
     J.mask = D.cap - 1;
@@ -107,7 +111,7 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.levels = D.levels;
     J.max_passes = D.max_passes;
     J.flags = A.flags;
-    J.timeout_ns = kBatchBarrierTimeoutNs;
+    J.timeout_ns = A.timeout_ns;
     J.trace = nullptr;
     return J;
 }
@@ -339,6 +343,8 @@ dfamin_status build_schedule(int32_t count, const int64_t* state_off, const int3
         D.o_lst_rst = L.lst_rst; D.o_lead = L.lead; D.o_lead_slot = L.lead_slot; D.o_stg = L.stg;
         D.o_table = L.table; D.o_sig = L.sig; D.o_cl = L.cl; D.o_cl_letter = L.cl_letter;
         D.o_naive = L.naive_new;
+        D.o_spl = L.spl;
+        D.o_cln = L.cln;
         off = align_up(off + L.total, A);
     }
     P->ws_bytes = off;
@@ -457,6 +463,8 @@ dfamin_status launch_batch(const dfamin_batch_plan_s& P, const BatchDesc* d_desc
     A.cta_cnt = (int32_t*)(base + P.off_cta);
     A.flags = P.opt.flags & ~DFAMIN_FLAG_TRACE;
     A.algo = P.opt.algorithm;
+    A.timeout_ns = P.opt.barrier_timeout_us > 0 ? 1000ll * P.opt.barrier_timeout_us
+                                                : kBatchBarrierTimeoutNs;
     void* args[] = {&A};
     if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(P.grid),
                                              dim3(kTeamThreads), args, P.dsmem, stream),
@@ -557,6 +565,16 @@ DFAMIN_API dfamin_status dfamin_minimize_batch(int32_t num_dfas, const int64_t* 
                                                size_t workspace_bytes, int32_t* status,
                                                dfamin_stream_t stream)
 {
+    // the descriptor table is copied from host memory that lives only during this call, so a
+    // captured copy would replay from freed memory: refuse capture (plans are the capturable form)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!cuda_ok(cudaStreamIsCapturing((cudaStream_t)stream, &cap), "cudaStreamIsCapturing"))
+        return DFAMIN_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "dfamin_minimize_batch: the stream is capturing; use a batch plan in graphs");
+        return DFAMIN_EINVAL;
+    }
     dfamin_batch_plan_s P;
     size_t desc_bytes = 0;
     dfamin_status st = one_shot_layout(num_dfas, state_off, k, delta_off, opt, &P, &desc_bytes);

@@ -192,6 +192,8 @@ void bind_dfa_arrays(Job& J, unsigned char* region, const DfaLayout& d)
     J.lead_slot = (uint32_t*)(region + d.lead_slot);
     J.stg = (int32_t*)(region + d.stg);
     J.naive_new = (int32_t*)(region + d.naive_new);
+    J.spl = (int32_t*)(region + d.spl);
+    J.cln = (int32_t*)(region + d.cln);
     J.table = (unsigned long long*)(region + d.table);
     J.mask = d.cap - 1;
     J.sig = (int32_t*)(region + d.sig);
@@ -239,7 +241,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     J.max_passes = o.max_passes > 0 ? o.max_passes : (n < 0x7fffffff ? n + 1 : n);
     J.flags = o.flags;
     J.algo = o.algorithm;
-    J.timeout_ns = kBarrierTimeoutNs;
+    J.timeout_ns = o.barrier_timeout_us > 0 ? 1000ll * o.barrier_timeout_us : kBarrierTimeoutNs;
     if (o.flags & DFAMIN_FLAG_TRACE) {
         J.trace = (long long*)(base + L.trace);
         J.trace_cap = (DFAMIN_TRACE_BYTES / 8 - 1) / 2;

@@ -37,7 +37,7 @@ inline dfamin_status check_options(const dfamin_options& o)
         return DFAMIN_EINVAL;
     if (o.algorithm != DFAMIN_ALG_SIGNATURE && o.algorithm != DFAMIN_ALG_LEADER)
         return DFAMIN_EINVAL;
-    if (o.reserved) return DFAMIN_EINVAL;
+    if (o.barrier_timeout_us < 0) return DFAMIN_EINVAL;
     return DFAMIN_OK;
 }
 
@@ -52,7 +52,7 @@ inline size_t small_smem_bytes(int32_t n, uint32_t* cap_out)
 // Per-DFA arrays of the multi-CTA path, as byte offsets from the start of the DFA's region.
 struct DfaLayout {
     size_t block, lst_s, lst_slot, lst_rst, lead, lead_slot, stg, table, sig, cl, cl_letter,
-        naive_new;
+        naive_new, spl, cln;
     size_t total;
     uint32_t cap;       // group-table capacity (power of two)
     int levels;         // 1 + floor(log2 n) with the closure, else 1
@@ -78,6 +78,8 @@ inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays
         L.lead_slot = off; off = align_up(off + sizeof(uint32_t) * (size_t)n, A);
         L.stg = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
         L.naive_new = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
+        L.spl = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
+        L.cln = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
         L.table = off; off = align_up(off + sizeof(unsigned long long) * (size_t)L.cap, A);
         L.sig = off;
         off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);
@@ -92,6 +94,9 @@ inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays
 bool cuda_ok(cudaError_t e, const char* what);
 
 extern std::mutex g_mu;
+
+// Text of the calling thread's last failure (dfamin_last_cuda_error).
+extern thread_local char g_last_error[256];
 
 // Current device, its SM count and its per-block opt-in shared memory (cached per device).
 dfamin_status device_props(int* dev, int* sms, size_t* smem_optin);

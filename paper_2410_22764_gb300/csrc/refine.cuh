@@ -70,7 +70,9 @@ struct Ctrl {                      // zeroed by the host before every launch
     int min_n_rev;                 // n - (smallest rejecting state), 0 if none
     int ncl_letters;               // letters that get closure columns
     int nlead;                     // entries in the global leader list
-    int pad[7];
+    int pad0;
+    unsigned long long moved;      // states listed as moving so far (all rounds)
+    int pad[4];
 };
 
 struct Job {
@@ -108,6 +110,12 @@ struct Job {
                                          // per launch; null = round 1 by the general path
     int32_t algo;                        // DFAMIN_ALG_SIGNATURE or DFAMIN_ALG_LEADER
     int32_t* naive_new;                  // [n] leader mode: elected new leader per old leader
+    int32_t* spl;                        // [n] by leader id: last round in which the block lost
+                                         // members (any contents at launch: a stale value can
+                                         // only cause extra work)
+    int32_t* cln;                        // [n] by leader id: the round in which the block was
+                                         // found unable to split (written for every leader in
+                                         // every incremental round before it is read)
 };
 
 static __device__ __forceinline__ uint64_t gtimer()
@@ -562,6 +570,25 @@ static __device__ __forceinline__ void count_heads(bool head, int* s_heads)
     if ((threadIdx.x & 31u) == 0u && m) atomicAdd(s_heads, __popc(m));
 }
 
+// As append_moved, for a loop whose last iteration only some lanes of a warp reach.
+static __device__ __forceinline__ void append_moved_partial(const Job& J, int c0, bool moved, int s,
+                                                     uint32_t slot, int* s_cnt)
+{
+    const unsigned act = __activemask();
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(act, moved);
+    if (m == 0u) return;
+    const int first = __ffs(m) - 1;
+    int pos0 = 0;
+    if ((int)lane == first) pos0 = atomicAdd(s_cnt, __popc(m));
+    pos0 = __shfl_sync(act, pos0, first);
+    if (moved) {
+        const int pos = pos0 + __popc(m & ((1u << lane) - 1u));
+        J.lst_s[c0 + pos] = s;
+        J.lst_slot[c0 + pos] = slot;
+    }
+}
+
 // Appends (s, slot) for the lanes with `moved` set: one shared atomic per warp.
 static __device__ __forceinline__ void append_moved(const Job& J, int c0, bool moved, int s,
                                              uint32_t slot, int* s_cnt)
@@ -607,6 +634,7 @@ struct CtaCache {
     int gmin[kSlots];
     int row[kSlots][SS];
     int lkey[kLeaderCache];
+    int lcln[kLeaderCache];              // the leader's clean mark (incremental rounds)
     int lrow[kLeaderCache][SS];
 };
 
@@ -630,16 +658,22 @@ static __device__ void cache_clear(CtaCache<SS>& C)
 
 template <int KC>
 static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s_claims, int* s_cnt,
-                                     CtaCache<RowOf<KC>::SS>& C, int* s_heads)
+                                     CtaCache<RowOf<KC>::SS>& C, int* s_heads, int pass,
+                                     bool incr)
 {
     constexpr int SS = RowOf<KC>::SS;
     constexpr int kSlots = CtaCache<SS>::kSlots;
     // software pipeline: block[s] and the successor row of the next state are in flight while
-    // the current state is processed
+    // the current state is processed (in incremental rounds rows are read only when needed)
     int nL = 0, nr[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) nr[c] = 0;
     {
         const int s = c0 + threadIdx.x;
-        if (s < c1) { nL = ld_blk(&J.block[s]); load_succ<KC>(J.delta, s, nr); }
+        if (s < c1) {
+            nL = ld_blk(&J.block[s]);
+            if (!incr) load_succ<KC>(J.delta, s, nr);
+        }
     }
     for (int base = c0; base < c1; base += blockDim.x) {
         const int s = base + threadIdx.x;
@@ -650,26 +684,35 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         if (DFAMIN_PREFETCH) {
             if (s + (int)blockDim.x < c1) {
                 nL = ld_blk(&J.block[s + blockDim.x]);
-                load_succ<KC>(J.delta, s + blockDim.x, nr);
+                if (!incr) load_succ<KC>(J.delta, s + blockDim.x, nr);
             }
         } else if (s < c1) {
             L = ld_blk(&J.block[s]);
-            load_succ<KC>(J.delta, s, r);
+            if (!incr) load_succ<KC>(J.delta, s, r);
         }
-        bool moved = false, fill = false, lfill = false;
+        bool moved = false, fill = false, lfill = false, lclean = false;
         uint32_t slot = 0;
         uint64_t h = 0;
         int row[SS], lr[SS];
         count_heads(s < c1 && L == s, s_heads);
-        if (s < c1 && L != s && row_ok<KC>(J, r)) {
+        bool visit = s < c1 && L != s;
+        if (visit) {
             const int li = L & (kLeaderCache - 1);
             if (C.lkey[li] == L) {
+                lclean = incr && C.lcln[li] == pass;
+                if (!lclean) {
 #pragma unroll
-                for (int c = 0; c < SS; ++c) lr[c] = C.lrow[li][c];
+                    for (int c = 0; c < SS; ++c) lr[c] = C.lrow[li][c];
+                }
             } else {
-                load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
+                lclean = incr && __ldcg(&J.cln[L]) == pass;
+                if (!lclean) load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
                 lfill = true;
             }
+            if (lclean) visit = false;
+            else if (incr) load_succ<KC>(J.delta, s, r);
+        }
+        if (visit && row_ok<KC>(J, r)) {
 #pragma unroll
             for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
             row[KC] = L;
@@ -712,23 +755,108 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         if (lfill) {
             const int li = L & (kLeaderCache - 1);
             if (atomicCAS(&C.lkey[li], -1, L) == -1) {
+                C.lcln[li] = lclean ? pass : 0;
+                if (!lclean) {
 #pragma unroll
-                for (int c = 0; c < SS; ++c) C.lrow[li][c] = lr[c];
+                    for (int c = 0; c < SS; ++c) C.lrow[li][c] = lr[c];
+                }
             }
         }
         __syncthreads();                              // fills visible to the next tile
     }
 }
 
+// ---- incremental rounds.  After a signature round every member of a block B has the same
+// row as B's leader (that is how the round grouped them), and the leader's row of that round is
+// in sig[] (published by the leader, or stored by it when it moved).  In the next round the
+// entry of letter a can change only if the block it names lost members in the round just done
+// (spl[] of that block's leader).  So a leader whose stored row names no such block has the same
+// row again, and so has every member of its block: the block cannot split this round and its
+// members are not visited (cln[leader] = pass tells them).  Only the other blocks are refined
+// as usual.  Same partition and same pass count as a full round.
+//
+// Runtime-width rows ([head, b_0 .. b_{ncols-1}], int4 chunks): is the stored row of leader s
+// stale this round?  Writes s's clean mark either way.
+static __device__ bool stored_row_dirty(const Job& J, int s, int ncols, int pass)
+{
+    const int4* row = reinterpret_cast<const int4*>(J.sig + (int64_t)s * J.sig_stride);
+    bool dirty = false;
+    for (int v = 0; v * 4 <= ncols && !dirty; ++v) {
+        const int4 x = __ldcg(row + v);
+        const int e[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = 4 * v + j;               // entry i is column i - 1
+            if (i >= 1 && i <= ncols) dirty |= __ldcg(&J.spl[e[j]]) == pass - 1;
+        }
+    }
+    J.cln[s] = dirty ? 0 : pass;
+    return dirty;
+}
+
 // ---- phase A: every leader publishes its signature row.  Leaders are kept in a per-CTA list:
 // a leader stays a leader (it is the smallest state of its block and stays in its own group),
-// and every round adds the smallest states of its new groups.
+// and every round adds the smallest states of its new groups.  With `incr` (the previous round
+// was a signature round) a leader whose stored row is still valid marks its block clean instead.
 template <int KC>
-static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, int ncols)
+static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, int ncols,
+                                     int pass, bool incr)
 {
     const int gid = rank * (int)blockDim.x + (int)threadIdx.x, stride = T * (int)blockDim.x;
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
+        if (incr) {
+            // U leaders per thread at a time, every load of a stage issued before any use: the
+            // test is a chain of dependent reads (list, old row, spl, then delta and gathers)
+            constexpr int U = KC <= 2 ? 4 : (KC <= 3 ? 2 : 1);
+            constexpr int NB = RowOf<KC>::NB;
+            for (int i0 = gid; i0 < nlead; i0 += U * stride) {
+                int sv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * stride;
+                    sv[u] = i < nlead ? __ldcg(&J.lead[i]) : -1;
+                }
+                int old[U][4 * NB];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int4* p = reinterpret_cast<const int4*>(J.sig + (int64_t)max(sv[u], 0) * SS);
+#pragma unroll
+                    for (int v = 0; v < NB; ++v) {
+                        const int4 x = sv[u] >= 0 ? __ldcg(p + v) : make_int4(0, 0, 0, 0);
+                        old[u][4 * v] = x.x; old[u][4 * v + 1] = x.y;
+                        old[u][4 * v + 2] = x.z; old[u][4 * v + 3] = x.w;
+                    }
+                }
+                bool dirty[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    dirty[u] = false;
+                    if (sv[u] < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) dirty[u] |= __ldcg(&J.spl[old[u][c]]) == pass - 1;
+                }
+                int r[U][KC];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (sv[u] < 0) continue;
+                    J.cln[sv[u]] = dirty[u] ? 0 : pass;
+                    if (dirty[u]) load_succ<KC>(J.delta, sv[u], r[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (sv[u] < 0 || !dirty[u]) continue;
+                    int row[SS];
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[u][c]]);
+                    row[KC] = sv[u];
+#pragma unroll
+                    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                    store_row<SS>(J.sig, sv[u], row);
+                }
+            }
+            return;
+        }
         int ns = 0, nr[KC];
         if (gid < nlead) {
             ns = __ldcg(&J.lead[gid]);
@@ -759,6 +887,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
             // warp reads consecutive entries of every closure column instead of scattered ones
             for (int s = gid; s < J.n; s += stride) {
                 if (ld_blk(&J.block[s]) != s) continue;
+                if (incr && !stored_row_dirty(J, s, ncols, pass)) continue;
                 int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
                 for (int v0 = 0; v0 < nch; v0 += 4) {
                     int x[16];
@@ -774,6 +903,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
         }
         for (int i = gid; i < nlead; i += stride) {
             const int s = __ldcg(&J.lead[i]);
+            if (incr && !stored_row_dirty(J, s, ncols, pass)) continue;
             int4* out = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
             for (int v0 = 0; v0 < nch; v0 += 4) {
                 int x[16];
@@ -788,14 +918,143 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
     }
 }
 
+// A member s of leader L (row r = its successors) compares its signature with L's row; if they
+// differ, s is listed to be regrouped (signature mode: its row is stored and its first table
+// position returned in *slot) or elected (leader mode).  member_row issues the loads (the
+// leader's row and the successors' block ids), member_decide compares and lists; split so that
+// the loads of several members can be in flight together.
+template <int KC>
+static __device__ __forceinline__ void member_row(const Job& J, int L, const int (&r)[KC],
+                                                  int (&row)[RowOf<KC>::SS],
+                                                  int (&lr)[RowOf<KC>::SS])
+{
+    constexpr int SS = RowOf<KC>::SS;
+    load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
+    row[KC] = L;
+#pragma unroll
+    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+}
+
+template <int KC>
+static __device__ __forceinline__ bool member_decide(const Job& J, int s, int L,
+                                                     const int (&row)[RowOf<KC>::SS],
+                                                     const int (&lr)[RowOf<KC>::SS],
+                                                     uint32_t* slot)
+{
+    constexpr int SS = RowOf<KC>::SS;
+    bool same = true;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) same &= (row[c] == lr[c]);
+    if (same) return false;
+    if (J.algo == DFAMIN_ALG_LEADER) {
+        *slot = naive_elect(J, s, L);
+        return true;
+    }
+    // T(s) != T(leader): publish the row and list s with its first probe position; the inserts
+    // run afterwards, packed into full warps
+    uint64_t h = hash_begin(L);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
+    h = hash_final(h, L, J.flags);
+    store_row<SS>(J.sig, s, row);
+    *slot = (uint32_t)h & J.mask;
+    return true;
+}
+
+template <int KC>
+static __device__ __forceinline__ bool member_compare(const Job& J, int s, int L, const int (&r)[KC],
+                                                      uint32_t* slot)
+{
+    constexpr int SS = RowOf<KC>::SS;
+    int row[SS], lr[SS];
+    member_row<KC>(J, L, r, row, lr);
+    return member_decide<KC>(J, s, L, row, lr, slot);
+}
+
 // ---- phase B: members compare with their leader; those that differ are regrouped.
 // The loop is uniform across the CTA so that appends can be aggregated per warp.
 template <int KC>
 static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt,
-                              int* s_heads)
+                              int* s_heads, int pass, bool incr)
 {
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
+        if (incr) {
+            // 1. list the members of blocks that may split (their leader is not marked clean)
+            //    in this CTA's segment of stg (states) and lst_rst (leaders).  Pipeline: the
+            //    block id of the state after next and the clean mark of the next state's leader
+            //    are in flight while the current state is tested.
+            __shared__ int s_dcnt;
+            if (threadIdx.x == 0) s_dcnt = 0;
+            __syncthreads();
+            const int bd = (int)blockDim.x;
+            int Lc = -1, Cc = 0, Ln = -1;
+            {
+                const int s0 = c0 + (int)threadIdx.x;
+                if (s0 < c1) Lc = ld_blk(&J.block[s0]);
+                if (s0 + bd < c1) Ln = ld_blk(&J.block[s0 + bd]);
+                if (s0 < c1 && Lc != s0) Cc = __ldcg(&J.cln[Lc]);
+            }
+            for (int base = c0; base < c1; base += bd) {
+                const int s = base + (int)threadIdx.x;
+                const int L = Lc, C = Cc;
+                Lc = Ln;
+                Cc = 0;
+                if (s + bd < c1 && Lc != s + bd) Cc = __ldcg(&J.cln[Lc]);
+                Ln = s + 2 * bd < c1 ? ld_blk(&J.block[s + 2 * bd]) : -1;
+                count_heads(s < c1 && L == s, s_heads);
+                const bool visit = s < c1 && L != s && C != pass;
+                const unsigned m = __ballot_sync(0xffffffffu, visit);
+                if (m) {
+                    const unsigned lane = threadIdx.x & 31u;
+                    const int first = __ffs(m) - 1;
+                    int pos0 = 0;
+                    if ((int)lane == first) pos0 = atomicAdd(&s_dcnt, __popc(m));
+                    pos0 = __shfl_sync(0xffffffffu, pos0, first);
+                    if (visit) {
+                        const int pos = c0 + pos0 + __popc(m & ((1u << lane) - 1u));
+                        J.stg[pos] = s;
+                        J.lst_rst[pos] = (uint32_t)L;
+                    }
+                }
+            }
+            __syncthreads();                          // the list (global, this CTA's) is complete
+            // 2. the listed members, packed into full warps.  Pipeline: the list entry after next
+            //    and the next member's successors are in flight while the current one is tested.
+            const int dcnt = s_dcnt;
+            int s1 = -1, L1 = 0, s2 = -1, L2 = 0, r1[KC];
+            {
+                const int i = (int)threadIdx.x;
+                if (i < dcnt) { s1 = __ldcg(&J.stg[c0 + i]); L1 = (int)__ldcg(&J.lst_rst[c0 + i]); }
+                if (i + bd < dcnt) {
+                    s2 = __ldcg(&J.stg[c0 + i + bd]);
+                    L2 = (int)__ldcg(&J.lst_rst[c0 + i + bd]);
+                }
+                if (s1 >= 0) load_succ<KC>(J.delta, s1, r1);
+            }
+            for (int i = (int)threadIdx.x; i < dcnt; i += bd) {
+                const int sv = s1, Lv = L1;
+                int r[KC];
+#pragma unroll
+                for (int c = 0; c < KC; ++c) r[c] = r1[c];
+                s1 = s2;
+                L1 = L2;
+                if (s1 >= 0) load_succ<KC>(J.delta, s1, r1);
+                s2 = -1;
+                if (i + 2 * bd < dcnt) {
+                    s2 = __ldcg(&J.stg[c0 + i + 2 * bd]);
+                    L2 = (int)__ldcg(&J.lst_rst[c0 + i + 2 * bd]);
+                }
+                uint32_t slot = 0;
+                const bool moved = row_ok<KC>(J, r) && member_compare<KC>(J, sv, Lv, r, &slot);
+                // every lane of the warp is in the loop while any is: the loop bound is uniform
+                // per warp only up to the last iteration, so the append is warp-synchronous on
+                // the lanes still in it
+                append_moved_partial(J, c0, moved, sv, slot, s_cnt);
+            }
+        } else {
         int nL = 0, nr[KC];
         {
             const int s = c0 + threadIdx.x;
@@ -819,34 +1078,9 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             bool moved = false;
             uint32_t slot = 0;
             count_heads(s < c1 && L == s, s_heads);
-            if (s < c1 && L != s && row_ok<KC>(J, r)) {
-                int lr[SS];
-                load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
-                int row[SS];
-#pragma unroll
-                for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
-                row[KC] = L;
-#pragma unroll
-                for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-                bool same = true;
-#pragma unroll
-                for (int c = 0; c < KC; ++c) same &= (row[c] == lr[c]);
-                if (!same && J.algo == DFAMIN_ALG_LEADER) {
-                    slot = naive_elect(J, s, L);
-                    moved = true;
-                } else if (!same) {
-                    // T(s) != T(leader): publish the row and list s with its first probe
-                    // position; the inserts run below, packed into full warps
-                    uint64_t h = hash_begin(L);
-#pragma unroll
-                    for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
-                    h = hash_final(h, L, J.flags);
-                    store_row<SS>(J.sig, s, row);
-                    slot = (uint32_t)h & J.mask;
-                    moved = true;
-                }
-            }
+            if (s < c1 && L != s && row_ok<KC>(J, r)) moved = member_compare<KC>(J, s, L, r, &slot);
             append_moved(J, c0, moved, s, slot, s_cnt);
+        }
         }
         if (J.algo != DFAMIN_ALG_LEADER) {
             // ---- regroup the listed states: every lane of a warp has an insert to do
@@ -877,7 +1111,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
             if (s < c1) L = ld_blk(&J.block[s]);
             count_heads(s < c1 && L == s, s_heads);
             if (s < c1) {
-                if (L != s) {
+                if (L != s && (!incr || __ldcg(&J.cln[L]) != pass)) {
                     const int4* lrow =
                         reinterpret_cast<const int4*>(J.sig + (int64_t)L * J.sig_stride);
                     int4* mine = reinterpret_cast<int4*>(J.sig + (int64_t)s * J.sig_stride);
@@ -969,6 +1203,25 @@ static __device__ __forceinline__ void append_pair(const Job& J, int c0, int* cn
         const int pos = c0 + pos0 + __popc(m & ((1u << lane) - 1u));
         J.stg[pos] = s;
         J.lst_rst[pos] = slot;
+    }
+}
+
+// Phase C, for a mover s that leads its new group (signature rounds): the block s left lost
+// members this round (spl), and s's row must be in sig[] for the next round's incremental test.
+// Uncached members stored their rows already; a group entered through the CTA cache holds only
+// its representative's row, which equals s's (full-row equality), so it is copied.
+template <int SS>
+static __device__ __forceinline__ void new_leader_bookkeeping(const Job& J, int s, uint32_t gslot,
+                                                              int pass, bool cached_round)
+{
+    J.spl[__ldcg(&J.block[s])] = pass;                // before block[s] is overwritten
+    if (cached_round) {
+        const int rep = slot_rep(__ldcg(&J.table[gslot]));
+        if (rep != s) {
+            int row[SS];
+            load_row<SS>(J.sig, rep, row);
+            store_row<SS>(J.sig, s, row);
+        }
     }
 }
 
@@ -1089,9 +1342,14 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = 0x7fffffff;
             __syncthreads();
             bool bad = false;
+            // the next state's row is in flight while this one's successors are looked up
+            int nr[KC];
+            if (c0 + (int)threadIdx.x < c1) load_succ<KC>(J.delta, c0 + (int)threadIdx.x, nr);
             for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
                 int r[KC];
-                load_succ<KC>(J.delta, q, r);
+#pragma unroll
+                for (int c = 0; c < KC; ++c) r[c] = nr[c];
+                if (q + (int)blockDim.x < c1) load_succ<KC>(J.delta, q + (int)blockDim.x, nr);
                 int pat = is_accepting(J, q) ? 1 : 0;
 #pragma unroll
                 for (int c = 0; c < KC; ++c) {
@@ -1159,16 +1417,29 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     if (threadIdx.x == 0) s_claims = 0;
                     __syncthreads();
                     int mine = 0;
-                    // two states per thread per step: their gathers and atomics overlap
+                    // two states per thread per step: their gathers and atomics overlap; the
+                    // rows of the next step's states are in flight meanwhile
+                    const int bd = (int)blockDim.x;
+                    int nr[2][KC];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        if (c0 + (int)threadIdx.x + u * bd < c1)
+                            load_succ<KC>(J.delta, c0 + (int)threadIdx.x + u * bd, nr[u]);
                     for (int q0 = c0 + threadIdx.x; q0 < c1; q0 += 2 * blockDim.x) {
                         uint32_t code[2];
                         int qv[2] = {q0, q0 + (int)blockDim.x};
+                        int rr[2][KC];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) rr[u][c] = nr[u][c];
+                            if (qv[u] + 2 * bd < c1) load_succ<KC>(J.delta, qv[u] + 2 * bd, nr[u]);
+                        }
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             code[u] = 0;
                             if (qv[u] >= c1) continue;
-                            int r[KC];
-                            load_succ<KC>(J.delta, qv[u], r);
+                            const int (&r)[KC] = rr[u];
                             code[u] = (uint32_t)__ldcs(&pidx[qv[u]]);
 #pragma unroll
                             for (int c = 0; c < KC; ++c)
@@ -1195,17 +1466,29 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     // every group's smallest state leads it and lists its table word for reset
                     if (threadIdx.x == 0) s_rst = 0;
                     __syncthreads();
+                    // four states per thread per step; the next step's codes are in flight
+                    uint32_t ncv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = c0 + u * (int)blockDim.x + (int)threadIdx.x;
+                        ncv[u] = q < c1 ? __ldcs(&J.lst_slot[q]) : 0u;
+                    }
                     for (int b = c0; b < c1; b += 4 * (int)blockDim.x) {
                         int qv[4], mv[4];
                         uint32_t cv[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             qv[u] = b + u * (int)blockDim.x + (int)threadIdx.x;
-                            cv[u] = qv[u] < c1 ? __ldcs(&J.lst_slot[qv[u]]) : 0u;
+                            cv[u] = ncv[u];
                         }
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
                             mv[u] = qv[u] < c1 ? (int)__ldcg(&dtab[cv[u]]) : -1;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = qv[u] + 4 * (int)blockDim.x;
+                            ncv[u] = q < c1 ? __ldcs(&J.lst_slot[q]) : 0u;
+                        }
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             if (qv[u] < c1) J.block[qv[u]] = mv[u];
@@ -1406,12 +1689,24 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         const bool stable1 = (round1_done && round1_count1 == round1_count0) ||
                              (round2_done && round1_count2 == round1_count1) ||
                              (keys_done && count == keys_count0);
+        // rows of the last round are in sig[] for every leader once a signature round has run
+        // (not after the pattern, dense-code or key rounds)
+        bool have_rows = false;
+        unsigned long long moved_seen = 0, moved_last = 0;
         while (!stable1 && (leader_mode || count < n)) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
                 break;
             }
             ++passes;
+            // an incremental round pays off when few blocks can split: the states that moved in
+            // the last round mark their old blocks, and a block is revisited when its row names
+            // one of them, so with M movers and ncols columns about ncols * 2M / n of the blocks
+            // are revisited.  Below a quarter of that bound the round is incremental.
+            const bool incr = have_rows && !leader_mode && !(J.flags & DFAMIN_FLAG_FULL_ROUNDS) &&
+                              ((J.flags & DFAMIN_FLAG_INCREMENTAL_ROUNDS) ||
+                               moved_last * 4ull * (unsigned long long)max(ncols, 1) <=
+                                   (unsigned long long)n);
             // ---- phase A: empty the slots of last round's groups (listed in phase C by each
             //      group's smallest state), then leaders publish rows
             {
@@ -1422,7 +1717,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     else J.table[__ldcg(&J.lead_slot[i])] = kEmptySlot;
                 }
                 lead_reset_from = nlead;
-                phase_leaders<KC>(J, rank, T, nlead, ncols);
+                phase_leaders<KC>(J, rank, T, nlead, ncols, passes, incr);
             }
             __syncthreads();
             if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; s_heads = 0; }
@@ -1438,17 +1733,21 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 if (use_cache) {
                     cache_clear(cache);
                     __syncthreads();
-                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache, &s_heads);
+                    phase_members_cached<KC>(J, c0, c1, &s_claims, &s_cnt, cache, &s_heads,
+                                             passes, incr);
                 } else {
-                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads);
+                    phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads, passes,
+                                      incr);
                 }
             } else {
-                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads);
+                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads, passes, incr);
             }
             __syncthreads();
             {
                 const int cl = leader_mode ? s_cnt : s_claims;   // leader mode: moved states
                 if (threadIdx.x == 0 && cl) atomicAdd(&J.ctrl->claims, (unsigned long long)cl);
+                if (threadIdx.x == 0 && s_cnt)
+                    atomicAdd(&J.ctrl->moved, (unsigned long long)s_cnt);
                 if (threadIdx.x == 0) J.cta_cnt[rank] = s_heads;
             }
             if (!team_barrier(ts)) goto done;
@@ -1457,6 +1756,9 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             const unsigned long long claims_now = ld_acquire_u64(&J.ctrl->claims);
             const int new_groups = (int)(claims_now - claims_seen);
             claims_seen = claims_now;
+            const unsigned long long moved_now = ld_acquire_u64(&J.ctrl->moved);
+            moved_last = moved_now - moved_seen;
+            moved_seen = moved_now;
             if (new_groups == 0) {                    // partition unchanged: stable
                 heads_valid = true;
                 break;
@@ -1467,8 +1769,9 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             {
                 const int cnt = s_cnt;
                 if constexpr (KC > 0) {
+                    constexpr int SS = RowOf<KC>::SS;
                     extern __shared__ __align__(16) unsigned char dsm[];
-                    auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
+                    auto& cache = *reinterpret_cast<CtaCache<SS>*>(dsm);
                     if (use_cache) {
                         for (int ci = threadIdx.x; ci < CtaCache<RowOf<KC>::SS>::kSlots;
                              ci += blockDim.x)
@@ -1509,6 +1812,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                         }
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
+                            if (sv[u] >= 0 && mv[u] == sv[u] && !leader_mode)
+                                new_leader_bookkeeping<SS>(J, sv[u], gsv[u], passes, use_cache);
                             if (sv[u] >= 0) J.block[sv[u]] = mv[u];
                             append_pair(J, c0, &s_rst, sv[u] >= 0 && mv[u] == sv[u], sv[u],
                                         gsv[u]);
@@ -1525,8 +1830,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                             gs = J.lst_slot[c0 + i];
                             const int m = leader_mode ? ld_volatile(&J.naive_new[gs])
                                                       : slot_min(__ldcg(&J.table[gs]));
-                            J.block[s] = m;
                             lead = (m == s);
+                            // a new block: the block s left lost members this round
+                            if (lead && !leader_mode) J.spl[__ldcg(&J.block[s])] = passes;
+                            J.block[s] = m;
                         }
                         append_pair(J, c0, &s_rst, lead, s, gs);
                     }
@@ -1545,6 +1852,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             if (!team_barrier(ts)) goto done;
             trace_mark(J, tw, passes, 6);
             count = leader_mode ? ld_volatile(&J.ctrl->nlead) : count + new_groups;
+            have_rows = !leader_mode;
         }
         if (ld_volatile(&J.ctrl->status) != 0) goto done;
 
@@ -1575,11 +1883,17 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             for (int r = threadIdx.x; r < T; r += blockDim.x) total += __ldcg(&J.cta_cnt[r]);
             total = cta_sum(total);
         }
+        // the next step's block ids are in flight while this step is scanned
+        int4 nb = make_int4(0, 0, 0, 0);
+        if (c0 + 4 * (int)threadIdx.x + 3 < c1)
+            nb = __ldcg(reinterpret_cast<const int4*>(J.block + c0 + 4 * (int)threadIdx.x));
         for (int base = c0; base < c1; base += 4 * blockDim.x) {
             const int s = base + 4 * (int)threadIdx.x;
             int f[4] = {0, 0, 0, 0};
+            const int4 b = nb;
+            if (s + 4 * (int)blockDim.x + 3 < c1)
+                nb = __ldcg(reinterpret_cast<const int4*>(J.block + s + 4 * (int)blockDim.x));
             if (s + 3 < c1) {
-                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
                 f[0] = b.x == s; f[1] = b.y == s + 1; f[2] = b.z == s + 2; f[3] = b.w == s + 3;
             } else {
                 for (int j = 0; j < 4; ++j) f[j] = (s + j < c1) && (ld_blk(&J.block[s + j]) == s + j);
@@ -1594,10 +1908,23 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         // out_block is the caller's array (in a batch: at the DFA's offset), so its int4 access
         // is used only when it is 16-byte aligned; block[] is in the workspace (aligned)
         const bool out_aligned = ((uintptr_t)J.out_block & 15u) == 0;
-        for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += 4 * blockDim.x) {
+        const int step = 4 * (int)blockDim.x;
+        int4 pb = make_int4(0, 0, 0, 0), po = make_int4(0, 0, 0, 0);
+        {
+            const int s0 = c0 + 4 * (int)threadIdx.x;
+            if (s0 + 3 < c1 && out_aligned) {
+                pb = __ldcg(reinterpret_cast<const int4*>(J.block + s0));
+                po = __ldcg(reinterpret_cast<const int4*>(J.out_block + s0));
+            }
+        }
+        for (int s = c0 + 4 * (int)threadIdx.x; s < c1; s += step) {
+            // the next step's ids and ranks are in flight while this step's gathers run
+            const int4 b = pb, o = po;
+            if (s + step + 3 < c1 && out_aligned) {
+                pb = __ldcg(reinterpret_cast<const int4*>(J.block + s + step));
+                po = __ldcg(reinterpret_cast<const int4*>(J.out_block + s + step));
+            }
             if (s + 3 < c1 && out_aligned) {
-                const int4 b = __ldcg(reinterpret_cast<const int4*>(J.block + s));
-                const int4 o = __ldcg(reinterpret_cast<const int4*>(J.out_block + s));
                 int4 r;
                 r.x = b.x == s ? o.x : __ldcg(&J.out_block[b.x]);
                 r.y = b.y == s + 1 ? o.y : __ldcg(&J.out_block[b.y]);

@@ -24,6 +24,8 @@ FLAG_KEEP_IDENTITY = 1
 FLAG_HASH_BLOCK_ONLY = 2
 FLAG_HASH_CONSTANT = 4
 FLAG_TRACE = 8
+FLAG_FULL_ROUNDS = 16
+FLAG_INCREMENTAL_ROUNDS = 32
 TRACE_BYTES = 262144
 TRACE_PHASES = {0: "start", 1: "validate", 2: "init", 3: "closure", 4: "leaders",
                 5: "members", 6: "moves", 7: "count", 8: "canonical"}
@@ -67,7 +69,7 @@ class Options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("ctas", ctypes.c_int32),
                 ("smem_states", ctypes.c_int32), ("team_states", ctypes.c_int32),
-                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("algorithm", ctypes.c_int32), ("barrier_timeout_us", ctypes.c_int32)]
 
 
 def _load():
@@ -137,13 +139,15 @@ def status_string(code: int) -> str:
 
 
 def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: int = 0,
-            smem_states: int = 0, team_states: int = 0, leader: bool = False) -> Options:
+            smem_states: int = 0, team_states: int = 0, leader: bool = False,
+            barrier_timeout_us: int = 0) -> Options:
     o = Options()
     _lib.dfamin_default_options(ctypes.byref(o))
     o.closure = CLOSURE_ON if closure else CLOSURE_OFF
     o.max_passes, o.flags, o.ctas, o.smem_states = max_passes, flags, ctas, smem_states
     o.team_states = team_states
     o.algorithm = ALG_LEADER if leader else ALG_SIGNATURE
+    o.barrier_timeout_us = barrier_timeout_us
     return o
 
 

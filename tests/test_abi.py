@@ -70,7 +70,7 @@ def test_host_argument_checks_need_no_gpu(lib):
     bad.algorithm = 9
     assert L.dfamin_workspace_size(100, 2, ctypes.byref(bad), ctypes.byref(sz)) == lib.EINVAL
     bad = lib.options()
-    bad.reserved = 1
+    bad.barrier_timeout_us = -1
     assert L.dfamin_workspace_size(100, 2, ctypes.byref(bad), ctypes.byref(sz)) == lib.EINVAL
     # workspace sizes grow with n, and the closure needs more
     sizes = []

@@ -220,3 +220,33 @@ def test_one_shot_batch_call(dm, closure):
     nb, st = nb.cpu().numpy(), st.cpu().numpy()
     for i, (b, n_b, _) in enumerate(want):
         assert st[i] == 0 and nb[i] == n_b and np.array_equal(o[i], b)
+
+
+def test_one_shot_batch_call_refuses_stream_capture(dm):
+    # the one-shot call copies its table from host memory that dies with the call, so it must
+    # not be recorded into a graph: it returns EINVAL on a capturing stream and enqueues nothing
+    dfas = mixed_batch(14, count=6, max_n=3000)
+    want = oracle_results(dfas)
+    delta, acc, state_off, ks = dm.pack_batch(dfas)
+    dd = torch.from_numpy(delta).cuda()
+    aa = torch.from_numpy(acc.view(np.int32)).cuda()
+    ws = dm.Workspace()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dm.minimize_batch(state_off, ks, dd, aa, workspace=ws, stream=s)   # sizes the workspace
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            dm.minimize_batch(state_off, ks, dd, aa, workspace=ws, stream=s)
+        except dm.DfaminError as e:
+            err = e
+    assert err is not None and err.code == dm.EINVAL
+    assert "capturing" in dm.lib().dfamin_last_cuda_error().decode()
+    out, nb, st = dm.minimize_batch(state_off, ks, dd, aa, workspace=ws)
+    torch.cuda.synchronize()
+    o = np.split(out.cpu().numpy(), state_off[1:-1])
+    nb, st = nb.cpu().numpy(), st.cpu().numpy()
+    for i, (b, n_b, _) in enumerate(want):
+        assert st[i] == 0 and nb[i] == n_b and np.array_equal(o[i], b)

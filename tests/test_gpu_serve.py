@@ -65,6 +65,39 @@ def test_alone_and_in_mix_identical(mods):
         assert m.nblocks == wn and np.array_equal(m.out_block, want)
 
 
+def test_alone_and_in_mix_identical_at_served_stream_sizes(mods):
+    # the served-stream distribution at its full size range: n log-uniform 10^3 .. 4*10^6,
+    # k 2..8, half uniform random, half inflated (c = 4), the largest sizes drawn on purpose,
+    # and one path DFA of 65,536 states (escalated to the closure after its pass cap)
+    dfamin, serve = mods
+    rng = np.random.default_rng(5)
+    sizes = [4_000_000, 2_500_000] + [int(10 ** rng.uniform(3, np.log10(4e6))) for _ in range(14)]
+    dfas = []
+    for i, n in enumerate(sizes):
+        k = int(rng.integers(2, 9))
+        if i % 2 == 0:
+            dfas.append(I.random_dfa(n, k, 0.5, int(rng.integers(1 << 30))))
+        else:
+            dfas.append(I.inflated_dfa(max(1, n // 4), k, 4, 0.5, int(rng.integers(1 << 30)),
+                                       permute=False)[0])
+    dfas.insert(5, I.path_fib_dfa(65536))
+    alone = [solo(serve, d) for d in dfas]
+    srv = serve.Server(budget_bytes=48 << 30, streams=4)
+    reqs = []
+    for i, d in enumerate(dfas):
+        reqs.append(srv.submit(d.n, d.k, d.delta, d.accept))
+        if i % 2 == 1:
+            srv.step()
+    srv.drain()
+    assert srv.stats.escalated >= 1
+    for d, a, m in zip(dfas, alone, reqs):
+        assert a.status == 0 and m.status == 0
+        assert a.nblocks == m.nblocks and a.passes == m.passes
+        assert np.array_equal(a.out_block, m.out_block)
+        want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+        assert m.nblocks == wn and np.array_equal(m.out_block, want)
+
+
 def test_batches_overlap_on_device(mods):
     dfamin, serve = mods
     from oracle.path_depth import path_passes
