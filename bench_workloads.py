@@ -107,14 +107,6 @@ def run_path(args):
           1e3 / main["ms"], "minimizations/s", main["ms"], main["steps"], 3, extra)
 
 
-def _batch_inputs(kind):
-    ns, ks, ps, seeds = I.batch_sizes(4096, 1)
-    if kind == "4b":
-        cap = I.batch_cap_for_transitions(4096, 1, 200_000_000)
-        ns, ks, ps, seeds = I.batch_sizes(4096, 1, n_cap=cap)
-    return I.random_batch(ns, ks, ps, seeds)
-
-
 def _per_dfa_launches(delta, acc, state_off, ks, steps):
     """One dfamin_minimize_ex launch per DFA (each DFA's rows and bitmap 16-byte aligned)."""
     count, ns = ks.size, np.diff(state_off)
@@ -149,33 +141,95 @@ def _per_dfa_launches(delta, acc, state_off, ks, steps):
     return statistics.median(ts), out.cpu().numpy(), sc.cpu().numpy()
 
 
+def _graph_of(fn, stream):
+    """fn captured into a CUDA graph on `stream` (after one uncaptured warm-up call)."""
+    with torch.cuda.stream(stream):
+        fn(stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn(stream)
+    return g
+
+
 def run_batch(args, kind):
-    delta, acc, state_off, ks = _batch_inputs(kind)
-    plan = dfamin.BatchPlan(state_off, ks, dfamin.options())
+    """One persistent launch per batch, replayed from a CUDA graph, with the options the
+    autotuner picks (timed candidates, cached per GPU and shape bucket), against the default
+    options and against one plain launch per DFA (4b).  Under torchrun the batch is sharded:
+    every rank generates and minimizes its size-balanced share of the 4,096 DFAs (no collective
+    on the data path) and the time is the slowest rank's."""
+    from paper_2410_22764_gb300 import autotune, multi
+    rank, world, local = bench.dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    ns, ks_all, ps, seeds = I.batch_sizes(4096, 1)
+    if kind == "4b":
+        cap = I.batch_cap_for_transitions(4096, 1, 200_000_000)
+        ns, ks_all, ps, seeds = I.batch_sizes(4096, 1, n_cap=cap)
+    mine = multi.shard_batch(ns, ks_all, world)[rank]
+    delta, acc, state_off, ks = I.random_batch(ns[mine], ks_all[mine], ps[mine], seeds[mine])
     dd = torch.from_numpy(delta).cuda()
     aa = torch.from_numpy(acc.view(np.int32)).cuda()
-    ws = dfamin.Workspace()
-    out = torch.empty(plan.states, dtype=torch.int32, device="cuda")
-    per = torch.zeros((3, plan.count), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    fn = lambda: plan.run(dd, aa, workspace=ws, out_block=out, per_dfa=per)  # noqa: E731
+    t0 = time.perf_counter()
+    tuned_opt, timings = autotune.tune_batch(state_off, ks, dd, aa)
+    tune_s = time.perf_counter() - t0
     steps = max(3, min(args.steps, 10 if kind == "4b" else 5))
-    ts = _time_steps(fn, steps, max(3, args.warmup), flush)
-    p = per.cpu().numpy()
-    assert (p[2] == 0).all()
-    ms = statistics.median(ts)
+    warm = max(3, args.warmup)
+    side = torch.cuda.Stream()
+    res, ref = {}, None
+    for name, opt in (("default", dfamin.options()), ("tuned", tuned_opt)):
+        plan = dfamin.BatchPlan(state_off, ks, opt)
+        ws = dfamin.Workspace()
+        out = torch.empty(plan.states, dtype=torch.int32, device="cuda")
+        per = torch.zeros((3, plan.count), dtype=torch.int32, device="cuda")
+
+        def launch(stream=None):
+            plan.run(dd, aa, workspace=ws, out_block=out, per_dfa=per, stream=stream)
+        plain = statistics.median(_time_steps(launch, steps, warm, flush))
+        g = _graph_of(launch, side)
+        graph = statistics.median(_time_steps(g.replay, steps, warm, flush))
+        p = per.cpu().numpy()
+        assert (p[2] == 0).all()
+        o = out.cpu().numpy()
+        if ref is None:
+            ref = (o, p)
+        else:
+            assert np.array_equal(o, ref[0]) and np.array_equal(p, ref[1])
+        res[name] = {"plain_launch_ms": plain, "graph_replay_ms": graph, "grid": plan.grid,
+                     "tickets": plan.tickets, "workspace_gb": plan.workspace_bytes / 1e9}
+        del g
+        plan.close()
+    ms = res["tuned"]["graph_replay_ms"]
+    p = ref[1]
     visits = int((np.diff(state_off) * ks.astype(np.int64) * p[1]).sum())
-    extra = {"batched_ms": ms, "dfas": int(plan.count), "states": int(plan.states),
-             "transitions": int(plan.transitions), "grid": plan.grid, "tickets": plan.tickets,
-             "dfas_per_s": plan.count / (ms / 1e3), "gpu_launches": steps,
-             "workspace_gb": plan.workspace_bytes / 1e9}
-    if kind == "4b":
+    # job-wide: the slowest rank's time, every rank's edge visits
+    ms, visits = multi.aggregate(ms, float(visits), pg, torch.device("cuda", local))
+    best = json.loads(min(timings, key=timings.get))
+    extra = {"batched_ms": ms, "dfas": 4096, "states": int(ns.sum()),
+             "transitions": int(np.sum(ns * ks_all.astype(np.int64))),
+             "dfas_per_s": 4096 / (ms / 1e3), "gpu_launches": steps,
+             "tuned_knobs": best, "tuning_s": tune_s, "tuning_candidates": len(timings),
+             "default": res["default"], "tuned": res["tuned"],
+             "tuned_vs_default": res["default"]["graph_replay_ms"] / res["tuned"]["graph_replay_ms"]}
+    if world > 1:
+        extra.update({"n_gpus": world, "scaling": "strong",
+                      "parallelism": f"batch sharded over {world} ranks (size-balanced)",
+                      "rank0_dfas": int(mine.size)})
+    if kind == "4b" and world == 1:
         pms, pout, psc = _per_dfa_launches(delta, acc, state_off, ks, 2)
-        assert np.array_equal(pout, out.cpu().numpy()) and np.array_equal(psc[:, 0], p[0])
+        assert np.array_equal(pout, ref[0]) and np.array_equal(psc[:, 0], p[0])
         extra.update({"per_dfa_launches_ms": pms, "batched_speedup": pms / ms})
     desc = ("4,096 random DFAs, n log-uniform 100..1e6, k 2..26, p 0.1..0.9, seed 1" +
-            (", n capped so that sum n*k = 2e8" if kind == "4b" else ", as drawn"))
-    _line(desc, visits / (ms / 1e3), "edge-visits/s", ms, steps, max(3, args.warmup), extra)
+            (", n capped so that sum n*k = 2e8" if kind == "4b" else ", as drawn") +
+            "; one persistent launch replayed from a CUDA graph with autotuned options")
+    if rank == 0:
+        _line(desc, visits / (ms / 1e3), "edge-visits/s", ms, steps, warm, extra)
+    if pg:
+        pg.destroy_process_group()
 
 
 def _serve_pool(pool, seed=5):
@@ -197,44 +251,104 @@ def _serve_pool(pool, seed=5):
     return out
 
 
-def run_serve(args):
+def _latency_stats(lat, t_elapsed, R, rate):
+    lat = np.asarray(lat)
+    return {"rate_req_per_s": rate, "dfas_per_s": R / t_elapsed,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+
+def _serve_batched(reqs, rate, max_work):
     from paper_2410_22764_gb300 import serve
-    pool = _serve_pool(64)
-    R = args.requests
-    stream_reqs = [pool[i % len(pool)] for i in range(R)]
-
-    def go(rate):
-        srv = serve.Server(budget_bytes=48 << 30, streams=4)
-        rng = np.random.default_rng(11)
-        gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
-        t0 = time.perf_counter()
-        arrive = t0 + np.cumsum(gaps)
-        i = 0
-        while i < R or not srv.idle():
-            now = time.perf_counter()
-            while i < R and arrive[i] <= now:
-                d = stream_reqs[i]
-                srv.submit(d.n, d.k, d.delta, d.accept, arrival=float(arrive[i]))
-                i += 1
-            if not srv.step():
-                time.sleep(20e-6)
-        t1 = time.perf_counter()
-        lat = np.array([r.latency for r in srv.completed if r.status == 0])
-        bad = sum(1 for r in srv.completed if r.status != 0)
-        return {"rate_req_per_s": rate, "dfas_per_s": R / (t1 - t0),
-                "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "failed": bad,
+    R = len(reqs)
+    srv = serve.Server(budget_bytes=48 << 30, streams=4, max_batch_work=max_work)
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(gaps)
+    i = 0
+    while i < R or not srv.idle():
+        now = time.perf_counter()
+        while i < R and arrive[i] <= now:
+            d = reqs[i]
+            srv.submit(d.n, d.k, d.delta, d.accept, arrival=float(arrive[i]))
+            i += 1
+        if not srv.step():
+            time.sleep(20e-6)
+    t1 = time.perf_counter()
+    lat = [r.latency for r in srv.completed if r.status == 0]
+    out = _latency_stats(lat, t1 - t0, R, rate)
+    out.update({"failed": sum(1 for r in srv.completed if r.status != 0),
                 "batches": srv.stats.batches, "max_inflight": srv.stats.max_inflight,
-                "max_device_overlap": srv.max_device_overlap(), "escalated": srv.stats.escalated}
+                "max_device_overlap": srv.max_device_overlap(),
+                "escalated": srv.stats.escalated})
+    return out
 
-    go(0)                                               # warm-up (allocator, plans)
-    sat = go(0)
-    runs = {"saturated": sat}
+
+def _serve_plain(reqs, rate, pass_cap=64):
+    """The same arrival stream served one request at a time, one dfamin_minimize_ex launch per
+    request (plus a closure rerun when the pass cap is hit, as the batching server does):
+    pinned host copy, H2D, the launch, D2H, in arrival order on one stream."""
+    R = len(reqs)
+    s = torch.cuda.Stream()
+    ws = dfamin.Workspace()
+    sc = torch.zeros(3, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(gaps)
+    lat, failed, escalated = [], 0, 0
+    with torch.cuda.stream(s):
+        for i, d in enumerate(reqs):
+            while time.perf_counter() < arrive[i]:
+                time.sleep(20e-6)
+            hd = torch.from_numpy(np.ascontiguousarray(d.delta, np.int32)).pin_memory()
+            ha = torch.from_numpy(np.ascontiguousarray(d.accept, np.uint32).view(np.int32)).pin_memory()
+            dd = hd.to("cuda", non_blocking=True)
+            aa = ha.to("cuda", non_blocking=True)
+            out = torch.empty(d.n, dtype=torch.int32, device="cuda")
+            dfamin.minimize_ex(d.n, d.k, dd, aa, opt=dfamin.options(max_passes=pass_cap),
+                               workspace=ws, out_block=out, scalars=sc, stream=s)
+            st = int(sc[2].item())
+            if st == dfamin.ENOCONVERGE:
+                escalated += 1
+                dfamin.minimize_ex(d.n, d.k, dd, aa, opt=dfamin.options(closure=True),
+                                   workspace=ws, out_block=out, scalars=sc, stream=s)
+                st = int(sc[2].item())
+            host = out.cpu()
+            del host
+            if st != 0:
+                failed += 1
+            lat.append(time.perf_counter() - arrive[i])
+    t1 = time.perf_counter()
+    out = _latency_stats(lat, t1 - t0, R, rate)
+    out.update({"failed": failed, "escalated": escalated})
+    return out
+
+
+def run_serve(args):
+    pool = _serve_pool(args.serve_pool)
+    R = args.requests
+    pick = np.random.default_rng(7).integers(0, len(pool), size=R)
+    reqs = [pool[int(i)] for i in pick]
+    W = args.max_batch_work
+    _serve_batched(reqs[: min(R, 200)], 0, W)          # warm-up (allocator, plans, kernels)
+    sat = _serve_batched(reqs, 0, W)
+    batched = {"saturated": sat}
+    plain_sat = _serve_plain(reqs, 0)
+    plain = {"saturated": plain_sat}
     for rho in (0.5, 0.8, 0.95):
-        runs[f"rho_{rho}"] = go(rho * sat["dfas_per_s"])
-    _line(f"served Poisson stream, {R} requests drawn from a pool of 64 DFAs (n log-uniform "
-          "1e3..4e6, k 2..8, 50% random / 50% inflated c=4, 5% path n=65536), HBM budget 48 GB",
-          sat["dfas_per_s"], "DFAs/s", 1e3 / sat["dfas_per_s"], R, 1, {"serve": runs})
+        rate = rho * sat["dfas_per_s"]
+        batched[f"rho_{rho}"] = _serve_batched(reqs, rate, W)
+        plain[f"rho_{rho}"] = _serve_plain(reqs, rate)
+    _line(f"served Poisson stream, {R} requests drawn from a pool of {len(pool)} DFAs (n "
+          "log-uniform 1e3..4e6, k 2..8, 50% random / 50% inflated c=4, 5% path n=65536), HBM "
+          f"budget 48 GB, batches of at most {W} transitions", sat["dfas_per_s"], "DFAs/s",
+          1e3 / sat["dfas_per_s"], R, 1,
+          {"serve": batched, "plain_one_launch_per_request": plain,
+           "batched_vs_plain_saturated": sat["dfas_per_s"] / plain_sat["dfas_per_s"],
+           "rho_rates_from": "the batching server's saturated DFAs/s (both arms see the same "
+                             "arrival times)"})
 
 
 # Table 2 of the paper: name -> (N, |Sigma|, naivePR ms, sortPR ms, transPR ms); None = t/o or
@@ -296,21 +410,38 @@ def run_table2(args):
             if rounds > args.table2_max_rounds:
                 row[vname] = {"skipped": f"about {rounds} rounds"}
                 continue
+            budget = 0
             if closure:
+                # every column of every level when the workspace fits in device memory (less
+                # 2 GB), else a column budget that fits: each column holds one int per state
+                # twice (the column and its place in the signature rows)
                 need = dfamin.workspace_size(d.n, d.k, dfamin.options(closure=True))
-                free = torch.cuda.mem_get_info()[0]
-                if need > free - (2 << 30):
-                    row[vname] = {"enomem": f"workspace {need / 1e9:.0f} GB > free "
-                                            f"{free / 1e9:.0f} GB"}
-                    continue
-            opt = dfamin.options(closure=closure, leader=leader)
+                free = torch.cuda.mem_get_info()[0] - (2 << 30)
+                if need > free:
+                    base = dfamin.workspace_size(d.n, d.k,
+                                                 dfamin.options(closure=True, closure_columns=1))
+                    budget = int((free - base) // (8 * d.n)) + 1
+                    if budget < 1:
+                        row[vname] = {"enomem": f"workspace {base / 1e9:.0f} GB > free "
+                                                f"{free / 1e9:.0f} GB"}
+                        continue
+            opt = dfamin.options(closure=closure, leader=leader, closure_columns=budget)
             # runs of seconds are timed once, without a warm-up run of their own (the kernels
             # were loaded by the rows before)
             long = rounds > 100_000
             reps = 1 if long else 3
             ms, nb, ps, st = _timed_runs(d, dd, aa, opt, reps, 0 if long else 1)
             assert st == 0 and nb == N, (name, vname, st, nb)
+            # closed forms of the plain pass counts (pinned by the oracle at small sizes):
+            # signature rounds take N - 2 on cyclic Fib and n - 1 on B_n (Table 2, Sec. 4.2),
+            # the leader election one more (its final round changes nothing)
+            if not closure:
+                nbits = int(name[1:]) if name.startswith("B") else 0
+                want = (N - 2 if name.startswith("Fib") else nbits - 1) + (1 if leader else 0)
+                assert ps == want, (name, vname, ps, want)
             row[vname] = {"ms": ms, "iterations": ps, "steps": reps}
+            if budget:
+                row[vname]["closure_columns"] = budget
             if vname == "transPR":
                 total += ms
         rows.append(row)
@@ -366,7 +497,7 @@ def run_minimal(args):
 
 
 def run(args):
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(bench.dist_env()[2])
     if args.workload == "random1k":
         run_random1k(args)
     elif args.workload == "path":

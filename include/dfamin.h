@@ -85,6 +85,9 @@ typedef enum {
                                          block whose members' successors all lie in blocks that
                                          did not split in the previous round keeps its members;
                                          same partition, same pass count) */
+#define DFAMIN_FLAG_BATCH_FOUR_CTAS 64u /* batches (tuning): run the batch kernel built for four
+                                         resident CTAs per SM (64 registers a thread) instead of
+                                         three (80 registers); results are the same */
 #define DFAMIN_FLAG_INCREMENTAL_ROUNDS 32u /* testing: every signature round that follows another
                                          one is incremental, however many states moved (the
                                          default chooses by that number).  FULL_ROUNDS wins if
@@ -115,6 +118,13 @@ typedef struct {
                             stays usable).  Meant for tests of that failure path: a bound of a
                             few microseconds makes a multi-CTA call fail without any fault.
                             One-CTA calls (small DFAs) have no such wait */
+    int32_t closure_columns; /* closure: 0 = build every column (floor(log2 n) levels of every
+                            letter); otherwise at most this many columns, level by level, and the
+                            workspace shrinks to match.  Any subset of the closed alphabet gives
+                            the same state equivalence (every added letter is a word over the
+                            original alphabet), so fewer columns never change the partition, only
+                            the number of passes (between the full closure's and the plain
+                            count) */
 } dfamin_options;
 
 /* Fills *opt with the defaults (closure off, automatic tuning). */
@@ -154,6 +164,34 @@ dfamin_status dfamin_minimize_ex(int32_t n, int32_t k, const int32_t *delta,
                                  const dfamin_options *opt, void *workspace,
                                  size_t workspace_bytes, int32_t *passes, int32_t *status,
                                  dfamin_stream_t stream);
+
+/*
+ * dfamin_minimize_from_host - the same minimization as dfamin_minimize_ex, end to end from HOST
+ * arrays: the rows and the bitmap are read from host memory and the labels and scalars are
+ * written back to it, all in stream order on `stream`.
+ *   h_delta     host int32 [n*k] (state-major, as for dfamin_minimize_ex); h_accept host uint32
+ *               bitmap [(n+31)/32]; h_out_block host int32 [n] (canonical labels);
+ *   h_scalars   host int32 [3]: nblocks (or -status), passes, status.
+ *   workspace   DEVICE memory of dfamin_minimize_from_host_workspace_size() bytes, 256-byte
+ *               aligned: the device copies of the inputs and outputs and the workspace of the
+ *               minimization.
+ * With page-locked host arrays (cudaHostAlloc, cudaHostRegister) the call is asynchronous and
+ * moves data with no separate copy where it can: the bitmap is copied first, then the first
+ * round reads every row straight from host memory (its only input besides the bitmap) while it
+ * computes, storing the device copy that later rounds read, and the last pass writes the labels
+ * and the scalars straight to host memory.  (That applies to DFAs solved by the multi-CTA
+ * kernel with 1..8 letters and no closure; in every other case, and for pageable host arrays,
+ * the arrays are copied before and after the kernel on the stream, and pageable arrays make the
+ * call return only when its copies are done.)  The host arrays must stay valid, and h_delta
+ * unchanged, until the stream has passed the call.
+ */
+dfamin_status dfamin_minimize_from_host_workspace_size(int32_t n, int32_t k,
+                                                      const dfamin_options *opt, size_t *bytes);
+dfamin_status dfamin_minimize_from_host(int32_t n, int32_t k, const int32_t *h_delta,
+                                        const uint32_t *h_accept, int32_t *h_out_block,
+                                        int32_t *h_scalars, const dfamin_options *opt,
+                                        void *workspace, size_t workspace_bytes,
+                                        dfamin_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Batches: many DFAs minimized in one persistent launch (each exactly as dfamin_minimize_ex

@@ -5,7 +5,8 @@ The knobs change no result, only speed:
     kernels (``smem_states``: everything in shared memory up to 8,192 states, 16-bit ids in
     shared memory up to 65,535);
   * batches: the one-CTA limit (``smem_states``), the states per CTA when sizing a team
-    (``team_states``) and a cap on the grid (``ctas``).
+    (``team_states``), a cap on the grid (``ctas``) and the batch kernel's occupancy (three or
+    four resident CTAs per SM, ``flags``).
 With ``allow_leader=True`` a single DFA may also be given the leader election (Alg. 2 naivePR,
 ``algorithm=1``): the partition is the same, the round count is that algorithm's own.
 
@@ -22,6 +23,7 @@ import statistics
 import threading
 
 _lock = threading.Lock()
+FLAG_BATCH_FOUR_CTAS = 64          # include/dfamin.h: DFAMIN_FLAG_BATCH_FOUR_CTAS
 
 
 def cache_path() -> str:
@@ -73,6 +75,9 @@ def batch_candidates(sms: int) -> list[dict]:
         for team in (4096, 16384, 65536):
             out.append({"smem_states": small, "team_states": team})
     out.append({"smem_states": 2048, "team_states": 16384, "ctas": 2 * sms})
+    # the batch kernel built for four resident CTAs per SM (fewer registers, more spills)
+    for team in (4096, 16384, 65536):
+        out.append({"smem_states": 2048, "team_states": team, "flags": FLAG_BATCH_FOUR_CTAS})
     return out
 
 
@@ -139,6 +144,25 @@ def tune_single(n: int, k: int, delta, accept, closure: bool = False, retune: bo
     best, timings = choose(single_key(gpu, n, k, closure, allow_leader),
                            single_candidates(n, sms, allow_leader), measure, path, retune)
     return opts(best), timings
+
+
+def cached(key: str, path: str | None = None) -> dict | None:
+    """The stored best candidate for `key`, or None (no measurement)."""
+    with _lock:
+        data = _load(path or cache_path())
+    e = data.get(key)
+    return e["best"] if e else None
+
+
+def lookup_batch(state_off, ks, closure: bool = False, path: str | None = None):
+    """Options tuned earlier for a batch of this shape bucket on this GPU, or None.  Measures
+    nothing, so it is cheap enough for a serving loop."""
+    import numpy as np
+    from . import dfamin
+    gpu, _ = _gpu_name_and_sms()
+    ns = np.diff(np.asarray(state_off, dtype=np.int64))
+    best = cached(batch_key(gpu, ns.tolist(), list(ks), closure), path)
+    return None if best is None else dfamin.options(closure=closure, **best)
 
 
 def tune_batch(state_off, ks, delta, accept, closure: bool = False, retune: bool = False,

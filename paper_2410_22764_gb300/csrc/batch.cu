@@ -46,6 +46,7 @@ struct BatchDesc {             // one DFA, in ticket order
     uint32_t small_cap;        // shared table capacity (small path)
     uint32_t cap;              // global table capacity (team path)
     int32_t levels, sig_stride, max_passes;
+    int32_t cl_cols;           // closure columns its region holds
     int32_t cta_base;          // first entry of its per-CTA counts
     int32_t nonid_base;        // first entry of its identity-letter flags
     int32_t pat_base;          // first entry of its round-1 pattern minima, -1 = none
@@ -109,6 +110,7 @@ __device__ Job batch_job(const BatchArgs& A, const BatchDesc& D)
     J.sig_stride = D.sig_stride;
     J.cl = (int32_t*)(r + D.o_cl);
     J.levels = D.levels;
+    J.cl_cols = D.cl_cols;
     J.max_passes = D.max_passes;
     J.flags = A.flags;
     J.timeout_ns = A.timeout_ns;
@@ -126,7 +128,10 @@ __device__ __noinline__ void run_team(const Job& J, int rank, int T)
 
 __device__ __noinline__ void run_small(const Job& J, uint32_t cap) { small_minimize(J, cap); }
 
-__global__ void __launch_bounds__(kTeamThreads, 3) batch_kernel(BatchArgs A)
+// The batch kernel, compiled for MINB resident CTAs per SM: 3 (80 registers a thread) by
+// default, 4 (64 registers, more spills) with DFAMIN_FLAG_BATCH_FOUR_CTAS.  A tuning knob only.
+template <int MINB>
+__global__ void __launch_bounds__(kTeamThreads, MINB) batch_kernel(BatchArgs A)
 {
     __shared__ long long s_ticket;
     for (;;) {
@@ -190,6 +195,12 @@ struct dfamin_batch_plan_s {
 namespace {
 
 constexpr int kBatchSmallDefault = 2048;     // n up to this: one CTA in shared memory
+
+const void* batch_kernel_for(uint32_t flags)
+{
+    return (flags & DFAMIN_FLAG_BATCH_FOUR_CTAS) ? (const void*)batch_kernel<4>
+                                                 : (const void*)batch_kernel<3>;
+}
 
 // Plans keep their descriptor table in stream-ordered memory (cudaMallocAsync / cudaFreeAsync
 // on a library stream per device), so that creating or destroying a plan never waits for work
@@ -269,7 +280,7 @@ dfamin_status build_schedule(int32_t count, const int64_t* state_off, const int3
     }
     if (dsmem + 2048 > smem_optin) return DFAMIN_EINVAL;
     int per_sm = 0;
-    st = kernel_ctas_per_sm(dev, (const void*)batch_kernel, kTeamThreads, dsmem, &per_sm);
+    st = kernel_ctas_per_sm(dev, batch_kernel_for(o.flags), kTeamThreads, dsmem, &per_sm);
     if (st != DFAMIN_OK) return st;
     int grid_max = std::min(sms * per_sm, kMaxCtas);
     if (o.ctas > 0) grid_max = std::min(grid_max, o.ctas);
@@ -334,10 +345,11 @@ dfamin_status build_schedule(int32_t count, const int64_t* state_off, const int3
     P->zero_end = off;
     P->off_cta = off; off = align_up(off + sizeof(int32_t) * (size_t)team_sum, A);
     for (auto& D : P->desc) {
-        const DfaLayout L = make_dfa_layout(D.n, D.k, closure, !D.small);
+        const DfaLayout L = make_dfa_layout(D.n, D.k, closure, !D.small, o.closure_columns);
         D.region = (int64_t)off;
         D.cap = L.cap;
         D.levels = L.levels;
+        D.cl_cols = L.cols;
         D.sig_stride = L.sig_stride;
         D.o_block = L.block; D.o_lst_s = L.lst_s; D.o_lst_slot = L.lst_slot;
         D.o_lst_rst = L.lst_rst; D.o_lead = L.lead; D.o_lead_slot = L.lead_slot; D.o_stg = L.stg;
@@ -466,7 +478,7 @@ dfamin_status launch_batch(const dfamin_batch_plan_s& P, const BatchDesc* d_desc
     A.timeout_ns = P.opt.barrier_timeout_us > 0 ? 1000ll * P.opt.barrier_timeout_us
                                                 : kBatchBarrierTimeoutNs;
     void* args[] = {&A};
-    if (!cuda_ok(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(P.grid),
+    if (!cuda_ok(cudaLaunchCooperativeKernel(batch_kernel_for(P.opt.flags), dim3(P.grid),
                                              dim3(kTeamThreads), args, P.dsmem, stream),
                  "batch_kernel cooperative launch"))
         return DFAMIN_ECUDA;

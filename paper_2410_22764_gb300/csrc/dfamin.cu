@@ -143,7 +143,7 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
     L.pat = off; off = align_up(off + sizeof(int32_t) * (size_t)kPatMax, A);
     L.zero_end = off;
     L.dfa = off;
-    L.d = make_dfa_layout(n, k, o.closure == DFAMIN_CLOSURE_ON, true);
+    L.d = make_dfa_layout(n, k, o.closure == DFAMIN_CLOSURE_ON, true, o.closure_columns);
     off += L.d.total;
     L.trace = off;                          // the trace is the workspace's last bytes
     if (o.flags & DFAMIN_FLAG_TRACE) off += DFAMIN_TRACE_BYTES;
@@ -200,12 +200,58 @@ void bind_dfa_arrays(Job& J, unsigned char* region, const DfaLayout& d)
     J.sig_stride = d.sig_stride;
     J.cl = (int32_t*)(region + d.cl);
     J.levels = d.levels;
+    J.cl_cols = d.cols;
+}
+
+// End-to-end calls on host arrays: where the rows come from and where the labels go.  The
+// aliases are the device-visible addresses of page-locked host memory, or null; what cannot be
+// read or written in place by the kernel is copied in stream order around the launch.
+struct HostIo {
+    const int32_t* delta_h;         // host rows
+    const int32_t* delta_alias;
+    int32_t* out_h;                 // host labels
+    int32_t* out_alias;
+};
+
+// The device-visible address of page-locked host memory (cudaHostAlloc, cudaHostRegister),
+// or null for pageable memory.
+void* host_alias(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
+// Stages what the chosen kernel does not move itself: rows before the launch (in = true), labels
+// after it (in = false).
+dfamin_status host_io_copy(const HostIo* io, bool in, bool kernel_moves_it, int32_t n, int32_t k,
+                           int32_t* d_delta, int32_t* d_out, cudaStream_t stream)
+{
+    if (!io || kernel_moves_it) return DFAMIN_OK;
+    if (in) {
+        if (k > 0 && !cuda_ok(cudaMemcpyAsync(d_delta, io->delta_h,
+                                              sizeof(int32_t) * (size_t)n * (size_t)k,
+                                              cudaMemcpyHostToDevice, stream),
+                              "cudaMemcpyAsync(rows to device)"))
+            return DFAMIN_ECUDA;
+        return DFAMIN_OK;
+    }
+    return cuda_ok(cudaMemcpyAsync(io->out_h, d_out, sizeof(int32_t) * (size_t)n,
+                                   cudaMemcpyDeviceToHost, stream),
+                   "cudaMemcpyAsync(labels to host)")
+               ? DFAMIN_OK
+               : DFAMIN_ECUDA;
 }
 
 dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint32_t* accept,
                          int32_t* out_block, int32_t* nblocks, const dfamin_options& o,
                          void* ws, size_t ws_bytes, int32_t* passes, int32_t* status,
-                         cudaStream_t stream)
+                         cudaStream_t stream, const HostIo* io = nullptr)
 {
     if (n < 1 || n > (1 << 30) || k < 0 || (int64_t)n * (int64_t)k >= ((int64_t)1 << 40))
         return DFAMIN_EINVAL;
@@ -261,9 +307,12 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
         int per_sm = 0;
         st = kernel_ctas_per_sm(dev, (const void*)small_kernel, kThreads, smem, &per_sm);
         if (st != DFAMIN_OK) return st;
+        st = host_io_copy(io, true, false, n, k, (int32_t*)delta, out_block, stream);
+        if (st != DFAMIN_OK) return st;
         (void)cudaGetLastError();   // the check below must see this launch's error only
         small_kernel<<<1, kThreads, smem, stream>>>(J, scap);
-        return cuda_ok(cudaGetLastError(), "small_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
+        if (!cuda_ok(cudaGetLastError(), "small_kernel launch")) return DFAMIN_ECUDA;
+        return host_io_copy(io, false, false, n, k, (int32_t*)delta, out_block, stream);
     }
     // one CTA with 16-bit ids and delta in shared memory (no closure): when asked
     // (smem_states >= n), or by default when a round's shared-memory work is small
@@ -278,9 +327,12 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
             kernel_ctas_per_sm(dev, (const void*)medium_kernel, kMediumThreads, msmem, &per_sm) ==
                 DFAMIN_OK &&
             per_sm >= 1) {
+            st = host_io_copy(io, true, false, n, k, (int32_t*)delta, out_block, stream);
+            if (st != DFAMIN_OK) return st;
             (void)cudaGetLastError();
             medium_kernel<<<1, kMediumThreads, msmem, stream>>>(J);
-            return cuda_ok(cudaGetLastError(), "medium_kernel launch") ? DFAMIN_OK : DFAMIN_ECUDA;
+            if (!cuda_ok(cudaGetLastError(), "medium_kernel launch")) return DFAMIN_ECUDA;
+            return host_io_copy(io, false, false, n, k, (int32_t*)delta, out_block, stream);
         }
     }
     size_t dsmem = 0;
@@ -296,12 +348,51 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     const int64_t want = ((int64_t)n + 2 * kTeamThreads - 1) / (2 * kTeamThreads);
     if (o.ctas == 0 && want < ctas) ctas = (int)(want > 0 ? want : 1);
     if (ctas > max_ctas) ctas = max_ctas;
+    // end-to-end: round 1 of a compile-time alphabet reads every row itself (from host memory
+    // when the rows are page-locked and aligned for its vector loads), and the canonical pass
+    // writes the labels to page-locked host memory
+    bool rows_in_kernel = false, labels_in_kernel = false;
+    if (io) {
+        const bool pattern_round = L.d.levels == 1 && o.algorithm == DFAMIN_ALG_SIGNATURE &&
+                                   k >= 1 && k <= kPatMaxK;
+        const uintptr_t need = (k % 4 == 0) ? 16 : ((k % 2 == 0) ? 8 : 4);
+        rows_in_kernel = pattern_round && io->delta_alias &&
+                         ((uintptr_t)io->delta_alias % need) == 0;
+        labels_in_kernel = io->out_alias != nullptr;
+        if (rows_in_kernel) {
+            J.delta_host = io->delta_alias;
+            J.delta_fill = (int32_t*)delta;
+        }
+        if (labels_in_kernel) J.out_host = io->out_alias;
+    }
+    st = host_io_copy(io, true, rows_in_kernel, n, k, (int32_t*)delta, out_block, stream);
+    if (st != DFAMIN_OK) return st;
     void* args[] = {&J};
     if (!cuda_ok(cudaLaunchCooperativeKernel(kern, dim3(ctas), dim3(kTeamThreads), args, dsmem,
                                              stream),
                  "team_kernel cooperative launch"))
         return DFAMIN_ECUDA;
-    return DFAMIN_OK;
+    return host_io_copy(io, false, labels_in_kernel, n, k, (int32_t*)delta, out_block, stream);
+}
+
+// Workspace of an end-to-end call: device copies of the rows, the bitmap, the labels and the
+// scalars, then the workspace of the minimization itself.
+struct HostLayout {
+    size_t delta, accept, out, sc, ws, total;
+};
+
+HostLayout host_layout(int32_t n, int32_t k, const dfamin_options& o)
+{
+    HostLayout H{};
+    const size_t A = 256;
+    size_t off = 0;
+    H.delta = off; off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)k, A);
+    H.accept = off; off = align_up(off + sizeof(uint32_t) * (((size_t)n + 31) / 32), A);
+    H.out = off; off = align_up(off + sizeof(int32_t) * (size_t)n, A);
+    H.sc = off; off = align_up(off + 3 * sizeof(int32_t), A);
+    H.ws = off;
+    H.total = off + make_layout(n, k, o).total;
+    return H;
 }
 
 // Scratch of dfamin_minimize_static: a file-scope device array (no allocation call).  Host code
@@ -418,6 +509,61 @@ DFAMIN_API dfamin_status dfamin_minimize_static(int32_t n, int32_t k, const int3
     if (sa != DFAMIN_OK) return sa;
     return launch_one(n, k, delta, accept, out_block, nblocks, o, scratch,
                       (size_t)DFAMIN_STATIC_SCRATCH_BYTES, passes, status, (cudaStream_t)stream);
+}
+
+DFAMIN_API dfamin_status dfamin_minimize_from_host_workspace_size(int32_t n, int32_t k,
+                                                                   const dfamin_options* opt,
+                                                                   size_t* bytes)
+{
+    if (n < 1 || n > (1 << 30) || k < 0 || !bytes) return DFAMIN_EINVAL;
+    dfamin_options o;
+    dfamin_default_options(&o);
+    if (opt) o = *opt;
+    const dfamin_status st = check_options(o);
+    if (st != DFAMIN_OK) return st;
+    *bytes = host_layout(n, k, o).total;
+    return DFAMIN_OK;
+}
+
+DFAMIN_API dfamin_status dfamin_minimize_from_host(int32_t n, int32_t k, const int32_t* h_delta,
+                                                   const uint32_t* h_accept, int32_t* h_out_block,
+                                                   int32_t* h_scalars, const dfamin_options* opt,
+                                                   void* workspace, size_t workspace_bytes,
+                                                   dfamin_stream_t stream)
+{
+    if (n < 1 || n > (1 << 30) || k < 0) return DFAMIN_EINVAL;
+    if ((k > 0 && !h_delta) || !h_accept || !h_out_block || !h_scalars || !workspace)
+        return DFAMIN_EINVAL;
+    if (((uintptr_t)workspace & 255u) != 0) return DFAMIN_EINVAL;
+    dfamin_options o;
+    dfamin_default_options(&o);
+    if (opt) o = *opt;
+    dfamin_status st = check_options(o);
+    if (st != DFAMIN_OK) return st;
+    const HostLayout H = host_layout(n, k, o);
+    if (workspace_bytes < H.total) return DFAMIN_ENOMEM;
+    unsigned char* base = (unsigned char*)workspace;
+    int32_t* d_delta = (int32_t*)(base + H.delta);
+    uint32_t* d_acc = (uint32_t*)(base + H.accept);
+    int32_t* d_out = (int32_t*)(base + H.out);
+    int32_t* d_sc = (int32_t*)(base + H.sc);
+    // the bitmap first: round 1 looks up the acceptance of successors anywhere in it
+    if (!cuda_ok(cudaMemcpyAsync(d_acc, h_accept, sizeof(uint32_t) * (((size_t)n + 31) / 32),
+                                 cudaMemcpyHostToDevice, (cudaStream_t)stream),
+                 "cudaMemcpyAsync(bitmap to device)"))
+        return DFAMIN_ECUDA;
+    HostIo io{h_delta, (const int32_t*)host_alias(h_delta), h_out_block,
+              (int32_t*)host_alias(h_out_block)};
+    int32_t* sc_alias = (int32_t*)host_alias(h_scalars);
+    int32_t* sc = sc_alias ? sc_alias : d_sc;
+    st = launch_one(n, k, d_delta, d_acc, d_out, sc, o, base + H.ws, workspace_bytes - H.ws,
+                    sc + 1, sc + 2, (cudaStream_t)stream, &io);
+    if (st != DFAMIN_OK) return st;
+    if (!sc_alias && !cuda_ok(cudaMemcpyAsync(h_scalars, d_sc, 3 * sizeof(int32_t),
+                                              cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+                              "cudaMemcpyAsync(scalars to host)"))
+        return DFAMIN_ECUDA;
+    return DFAMIN_OK;
 }
 
 DFAMIN_API const char* dfamin_last_cuda_error(void) { return dfamin_host::g_last_error; }

@@ -37,7 +37,7 @@ inline dfamin_status check_options(const dfamin_options& o)
         return DFAMIN_EINVAL;
     if (o.algorithm != DFAMIN_ALG_SIGNATURE && o.algorithm != DFAMIN_ALG_LEADER)
         return DFAMIN_EINVAL;
-    if (o.barrier_timeout_us < 0) return DFAMIN_EINVAL;
+    if (o.barrier_timeout_us < 0 || o.closure_columns < 0) return DFAMIN_EINVAL;
     return DFAMIN_OK;
 }
 
@@ -56,16 +56,21 @@ struct DfaLayout {
     size_t total;
     uint32_t cap;       // group-table capacity (power of two)
     int levels;         // 1 + floor(log2 n) with the closure, else 1
+    int cols;           // closure columns held: k * (levels - 1), or the budget if smaller
     int sig_stride;     // ints per signature row
 };
 
-inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays)
+// col_budget: at most this many closure columns (0 = every column of every level).
+inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays,
+                                 int32_t col_budget = 0)
 {
     DfaLayout L{};
     const size_t A = 256;
     size_t off = 0;
     L.levels = closure ? floor_log2(n) + 1 : 1;
-    const int64_t kmax = (int64_t)k * L.levels;      // signature columns (upper bound)
+    const int64_t full = (int64_t)k * (L.levels - 1);
+    L.cols = (int)(col_budget > 0 && col_budget < full ? col_budget : full);
+    const int64_t kmax = (int64_t)k + L.cols;        // signature columns (upper bound)
     L.sig_stride = (int)((kmax + 1 + 3) / 4 * 4);
     L.cap = next_pow2_u32((uint64_t)n + (uint64_t)n / 2 + 64);
     L.cl_letter = off; off = align_up(off + sizeof(int32_t) * (size_t)(k > 0 ? k : 1), A);
@@ -85,7 +90,7 @@ inline DfaLayout make_dfa_layout(int32_t n, int32_t k, bool closure, bool arrays
         off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.sig_stride, A);
     }
     L.cl = off;
-    off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)k * (size_t)(L.levels - 1), A);
+    off = align_up(off + sizeof(int32_t) * (size_t)n * (size_t)L.cols, A);
     L.total = off;
     return L;
 }

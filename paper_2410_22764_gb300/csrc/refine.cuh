@@ -101,6 +101,7 @@ struct Job {
     Ctrl* ctrl;
     uint32_t mask;                       // table capacity - 1
     int32_t levels;                      // closure levels (1 = no closure)
+    int32_t cl_cols;                     // closure columns the workspace holds (the budget)
     int32_t max_passes;
     uint32_t flags;
     int64_t timeout_ns;
@@ -116,6 +117,12 @@ struct Job {
     int32_t* cln;                        // [n] by leader id: the round in which the block was
                                          // found unable to split (written for every leader in
                                          // every incremental round before it is read)
+    // end-to-end calls on page-locked host arrays (else null): round 1 reads every state's row
+    // from host memory once and stores the device copy (delta) that later rounds read; the
+    // canonical pass writes the labels to host memory
+    const int32_t* delta_host;           // [n*k] device-visible alias of the host rows
+    int32_t* delta_fill;                 // == delta, writable: the copy round 1 fills
+    int32_t* out_host;                   // [n] device-visible alias of the host labels
 };
 
 static __device__ __forceinline__ uint64_t gtimer()
@@ -413,6 +420,24 @@ static __device__ __forceinline__ void load_succ(const int32_t* __restrict__ del
     } else {
 #pragma unroll
         for (int c = 0; c < KC; ++c) r[c] = __ldcs(p + c);
+    }
+}
+
+// Stores the row of s (the device copy filled while reading rows from host memory).
+template <int KC>
+static __device__ __forceinline__ void store_succ(int32_t* delta, int s, const int (&r)[KC])
+{
+    int32_t* p = delta + (int64_t)s * KC;
+    if constexpr (KC % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < KC / 4; ++v)
+            reinterpret_cast<int4*>(p)[v] = make_int4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    } else if constexpr (KC % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < KC / 2; ++v) reinterpret_cast<int2*>(p)[v] = make_int2(r[2 * v], r[2 * v + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < KC; ++c) p[c] = r[c];
     }
 }
 
@@ -1255,7 +1280,13 @@ static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamS
     __syncthreads();
     int na = ncl, ncol = 0;
     for (int i = 1; i <= lv && na > 0; ++i) {
-        for (int r = 0; r < na; ++r) {
+        // column budget: a level that does not fit whole is built for its first letters only,
+        // and no level follows it (missing columns only cost rounds: every subset of the closed
+        // alphabet has the same state equivalence)
+        const int nb = min(na, J.cl_cols - ncol);
+        if (nb <= 0) break;
+        const bool truncated = nb < na;
+        for (int r = 0; r < nb; ++r) {
             const int a = sat ? s_act[r] : __ldcg(&J.cl_letter[r]);
             const int src = sat ? s_src[r] : (i == 1 ? -1 : ncol - na + r);
             const int32_t* prev = J.cl + (int64_t)src * n;
@@ -1277,7 +1308,7 @@ static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamS
                 if (__syncthreads_or(changed) && threadIdx.x == 0) J.nonid[a] = i + 1;
             }
         }
-        ncol += na;
+        ncol += nb;
         if (ts) {
             if (!team_barrier(*ts)) return -1;
         } else {
@@ -1287,11 +1318,11 @@ static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamS
         if (sat) {
             if (threadIdx.x == 0) {
                 int m = 0;
-                for (int r = 0; r < na; ++r) {
+                for (int r = 0; r < nb; ++r) {
                     const int a = s_act[r];
                     if (ld_volatile(&J.nonid[a]) == i + 1) {
                         s_act[m] = a;
-                        s_src[m] = ncol - na + r;
+                        s_src[m] = ncol - nb + r;
                         ++m;
                     }
                 }
@@ -1299,10 +1330,11 @@ static __device__ int closure_build(const Job& J, int c0, int c1, int ncl, TeamS
             }
             __syncthreads();
             // no letter changed at level i: the whole level repeats level i-1, drop it
-            if (s_na == 0) ncol -= na;
+            if (s_na == 0) ncol -= nb;
             na = s_na;
             __syncthreads();
         }
+        if (truncated) break;
     }
     return ncol;
 }
@@ -1342,14 +1374,18 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = 0x7fffffff;
             __syncthreads();
             bool bad = false;
-            // the next state's row is in flight while this one's successors are looked up
+            // the next state's row is in flight while this one's successors are looked up.
+            // From host memory (end-to-end calls) every row is read once here and stored to the
+            // device copy that the later rounds read.
+            const int32_t* rows = J.delta_host ? J.delta_host : J.delta;
             int nr[KC];
-            if (c0 + (int)threadIdx.x < c1) load_succ<KC>(J.delta, c0 + (int)threadIdx.x, nr);
+            if (c0 + (int)threadIdx.x < c1) load_succ<KC>(rows, c0 + (int)threadIdx.x, nr);
             for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
                 int r[KC];
 #pragma unroll
                 for (int c = 0; c < KC; ++c) r[c] = nr[c];
-                if (q + (int)blockDim.x < c1) load_succ<KC>(J.delta, q + (int)blockDim.x, nr);
+                if (q + (int)blockDim.x < c1) load_succ<KC>(rows, q + (int)blockDim.x, nr);
+                if (J.delta_host) store_succ<KC>(J.delta_fill, q, r);
                 int pat = is_accepting(J, q) ? 1 : 0;
 #pragma unroll
                 for (int c = 0; c < KC; ++c) {
@@ -1907,7 +1943,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         if (!team_barrier(ts)) goto done;
         // out_block is the caller's array (in a batch: at the DFA's offset), so its int4 access
         // is used only when it is 16-byte aligned; block[] is in the workspace (aligned)
-        const bool out_aligned = ((uintptr_t)J.out_block & 15u) == 0;
+        const bool out_aligned = ((uintptr_t)J.out_block & 15u) == 0 &&
+                                 ((uintptr_t)J.out_host & 15u) == 0;
         const int step = 4 * (int)blockDim.x;
         int4 pb = make_int4(0, 0, 0, 0), po = make_int4(0, 0, 0, 0);
         {
@@ -1930,11 +1967,15 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                 r.y = b.y == s + 1 ? o.y : __ldcg(&J.out_block[b.y]);
                 r.z = b.z == s + 2 ? o.z : __ldcg(&J.out_block[b.z]);
                 r.w = b.w == s + 3 ? o.w : __ldcg(&J.out_block[b.w]);
-                *reinterpret_cast<int4*>(J.out_block + s) = r;
+                // end-to-end calls: the labels go straight to host memory (the device array
+                // keeps the leaders' ranks, the only entries gathered here)
+                *reinterpret_cast<int4*>(J.out_host ? J.out_host + s : J.out_block + s) = r;
             } else {
                 for (int j = s; j < min(s + 4, c1); ++j) {
                     const int L = ld_blk(&J.block[j]);
-                    if (L != j) J.out_block[j] = __ldcg(&J.out_block[L]);
+                    const int v = __ldcg(&J.out_block[L]);
+                    if (J.out_host) J.out_host[j] = v;
+                    else if (L != j) J.out_block[j] = v;
                 }
             }
         }

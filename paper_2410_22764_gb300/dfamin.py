@@ -26,6 +26,7 @@ FLAG_HASH_CONSTANT = 4
 FLAG_TRACE = 8
 FLAG_FULL_ROUNDS = 16
 FLAG_INCREMENTAL_ROUNDS = 32
+FLAG_BATCH_FOUR_CTAS = 64
 TRACE_BYTES = 262144
 TRACE_PHASES = {0: "start", 1: "validate", 2: "init", 3: "closure", 4: "leaders",
                 5: "members", 6: "moves", 7: "count", 8: "canonical"}
@@ -39,6 +40,8 @@ ABI_FUNCTIONS = (
     "dfamin_status_string",
     "dfamin_last_cuda_error",
     "dfamin_minimize_static",
+    "dfamin_minimize_from_host",
+    "dfamin_minimize_from_host_workspace_size",
     "dfamin_batch_plan_create",
     "dfamin_batch_plan_destroy",
     "dfamin_batch_workspace_size",
@@ -69,7 +72,8 @@ class Options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("ctas", ctypes.c_int32),
                 ("smem_states", ctypes.c_int32), ("team_states", ctypes.c_int32),
-                ("algorithm", ctypes.c_int32), ("barrier_timeout_us", ctypes.c_int32)]
+                ("algorithm", ctypes.c_int32), ("barrier_timeout_us", ctypes.c_int32),
+                ("closure_columns", ctypes.c_int32)]
 
 
 def _load():
@@ -89,6 +93,12 @@ def _load():
     lib.dfamin_status_string.restype = ctypes.c_char_p
     lib.dfamin_minimize_static.argtypes = [i32, i32, p, p, p, p, ctypes.POINTER(Options), p, p, p]
     lib.dfamin_minimize_static.restype = ctypes.c_int
+    lib.dfamin_minimize_from_host.argtypes = [i32, i32, p, p, p, p, ctypes.POINTER(Options), p,
+                                              sz, p]
+    lib.dfamin_minimize_from_host.restype = ctypes.c_int
+    lib.dfamin_minimize_from_host_workspace_size.argtypes = [i32, i32, ctypes.POINTER(Options),
+                                                             ctypes.POINTER(sz)]
+    lib.dfamin_minimize_from_host_workspace_size.restype = ctypes.c_int
     lib.dfamin_batch_plan_create.argtypes = [i32, p, p, ctypes.POINTER(Options),
                                              ctypes.POINTER(ctypes.c_void_p)]
     lib.dfamin_batch_plan_destroy.argtypes = [p]
@@ -140,7 +150,7 @@ def status_string(code: int) -> str:
 
 def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: int = 0,
             smem_states: int = 0, team_states: int = 0, leader: bool = False,
-            barrier_timeout_us: int = 0) -> Options:
+            barrier_timeout_us: int = 0, closure_columns: int = 0) -> Options:
     o = Options()
     _lib.dfamin_default_options(ctypes.byref(o))
     o.closure = CLOSURE_ON if closure else CLOSURE_OFF
@@ -148,6 +158,7 @@ def options(closure: bool = False, max_passes: int = 0, flags: int = 0, ctas: in
     o.team_states = team_states
     o.algorithm = ALG_LEADER if leader else ALG_SIGNATURE
     o.barrier_timeout_us = barrier_timeout_us
+    o.closure_columns = closure_columns
     return o
 
 
@@ -225,6 +236,37 @@ def minimize_ex(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor, *,
     if rc:
         raise DfaminError(rc, "dfamin_minimize_ex")
     return Result(out_block, scalars)
+
+
+def minimize_from_host(n: int, k: int, delta: torch.Tensor, accept: torch.Tensor,
+                       out_block: torch.Tensor, scalars: torch.Tensor, *,
+                       opt: Options | None = None, workspace: Workspace | None = None,
+                       stream=None):
+    """Enqueue dfamin_minimize_from_host: ``delta`` (int32 [n*k]), ``accept`` (32-bit bitmap),
+    ``out_block`` (int32 [n]) and ``scalars`` (int32 [3] = nblocks, passes, status) are CPU
+    tensors (page-locked ones, e.g. ``pin_memory()``, for the asynchronous path); the workspace
+    is device memory."""
+    opt = opt or options()
+    for t in (delta, accept, out_block, scalars):
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError("host arrays must be contiguous CPU tensors")
+    if k > 0 and (delta.dtype != torch.int32 or delta.numel() != n * k):
+        raise ValueError("delta must be an int32 tensor of n*k entries")
+    if accept.element_size() != 4 or accept.numel() < (n + 31) // 32:
+        raise ValueError("accept must be a 32-bit bitmap of (n+31)//32 words")
+    if out_block.dtype != torch.int32 or out_block.numel() < n or scalars.numel() < 3:
+        raise ValueError("out_block int32 [n] and scalars int32 [3] expected")
+    need = ctypes.c_size_t(0)
+    rc = _lib.dfamin_minimize_from_host_workspace_size(n, k, ctypes.byref(opt), ctypes.byref(need))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize_from_host_workspace_size")
+    ws = (workspace or Workspace()).get(need.value)
+    rc = _lib.dfamin_minimize_from_host(
+        n, k, _ptr(delta) if k > 0 else ctypes.c_void_p(0), _ptr(accept), _ptr(out_block),
+        _ptr(scalars), ctypes.byref(opt), _ptr(ws), ctypes.c_size_t(ws.numel()),
+        _stream_handle(stream))
+    if rc:
+        raise DfaminError(rc, "dfamin_minimize_from_host")
 
 
 def read_trace(ws: Workspace, n: int, k: int, opt: Options):

@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import dfamin
+from . import autotune, dfamin
 
 
 @dataclass
@@ -76,15 +76,31 @@ class ServerStats:
 
 
 class Server:
+    """Continuous-batching server.
+
+    budget_bytes    device memory the requests in flight may hold together (admission bound)
+    streams         batches that may be in flight at once
+    max_batch       requests per batch at most
+    max_batch_work  transitions (sum of n*k) per batch at most, except that a batch always takes
+                    at least one request: a small bound keeps short requests from waiting behind
+                    one huge batch, and lets more batches overlap on the device
+    pass_cap        plain-refinement passes before a request is rerun on the closure
+    tuned           use batch options from the autotuner's cache when it has them for the
+                    batch's shape (a lookup, no measurement)
+    """
+
     def __init__(self, budget_bytes: int = 32 << 30, streams: int = 4, max_batch: int = 1024,
-                 pass_cap: int = 64, device: str | torch.device = "cuda", flags: int = 0):
+                 pass_cap: int = 64, device: str | torch.device = "cuda", flags: int = 0,
+                 max_batch_work: int = 1 << 62, tuned: bool = True):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.free = list(range(streams))
         self.max_batch = max_batch
+        self.max_batch_work = int(max_batch_work)
         self.pass_cap = pass_cap
         self.flags = flags
+        self.tuned = tuned
         self.pending: deque[Request] = deque()
         self.inflight: list[_Batch] = []
         self.used = 0
@@ -143,11 +159,15 @@ class Server:
             reqs = []
             head_closure = self.pending[0].closure
             budget_left = self.budget - self.used
+            work = 0
             while (self.pending and len(reqs) < self.max_batch
                    and self.pending[0].closure == head_closure
-                   and self.pending[0].nbytes <= budget_left):
+                   and self.pending[0].nbytes <= budget_left
+                   and (not reqs or work + self.pending[0].n * self.pending[0].k
+                        <= self.max_batch_work)):
                 r = self.pending.popleft()
                 budget_left -= r.nbytes
+                work += r.n * r.k
                 reqs.append(r)
             if reqs:
                 self._launch(reqs, head_closure)
@@ -171,6 +191,11 @@ class Server:
         delta, acc, state_off, ks = dfamin.pack_batch(reqs)
         opt = dfamin.options(closure=closure, max_passes=0 if closure else self.pass_cap,
                              flags=self.flags)
+        if self.tuned:
+            t = autotune.lookup_batch(state_off, ks, closure)
+            if t is not None:
+                opt.smem_states, opt.team_states, opt.ctas = t.smem_states, t.team_states, t.ctas
+                opt.flags |= t.flags
         plan = dfamin.BatchPlan(state_off, ks, opt)
         h_delta = torch.from_numpy(delta).pin_memory()
         h_acc = torch.from_numpy(acc.view(np.int32)).pin_memory()
