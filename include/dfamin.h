@@ -92,6 +92,16 @@ typedef enum {
                                          one is incremental, however many states moved (the
                                          default chooses by that number).  FULL_ROUNDS wins if
                                          both are set */
+#define DFAMIN_FLAG_MASKED_ROUNDS 128u /* testing: every signature round that follows another
+                                         one is letter-masked (compile-time alphabets k <= 8, no
+                                         closure): each leader marks the letters whose entry names
+                                         a block that split in the previous round, and members
+                                         gather only those letters (the others cannot differ from
+                                         the leader's).  By default a round is masked when members
+                                         outnumber leaders or few states moved, and the partition
+                                         has more than a few thousand blocks.  Same partition, same
+                                         pass count.  FULL_ROUNDS and INCREMENTAL_ROUNDS win if
+                                         set */
 
 /* Phase trace.  With DFAMIN_FLAG_TRACE the workspace grows by DFAMIN_TRACE_BYTES, and the last
  * DFAMIN_TRACE_BYTES of the required workspace receive int64 values: [0] = number of records,

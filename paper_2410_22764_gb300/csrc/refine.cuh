@@ -464,6 +464,18 @@ struct RowOf {
     static constexpr int NB = (KC + 3) / 4;
 };
 
+// Letter-masked rounds mark, in a leader's row, the entries that can change this round: bit 31
+// of b_a (block ids are below n < 2^31, so the bit is free).  A marked row is read only by the
+// round's members; every other reader of a leader's row takes the ids with the bit cleared.
+constexpr int kChanged = (int)0x80000000u;
+constexpr int kIdBits = 0x7fffffff;
+
+template <int KC>
+struct MaskOf {
+    static constexpr bool kFits = KC > 0;
+};
+
+// The first NB int4 of a row: a leader's successor ids (marks cleared).
 template <int SS, int NB>
 static __device__ __forceinline__ void load_row_prefix(const int32_t* sig, int s, int (&row)[SS])
 {
@@ -471,8 +483,33 @@ static __device__ __forceinline__ void load_row_prefix(const int32_t* sig, int s
 #pragma unroll
     for (int v = 0; v < NB; ++v) {
         const int4 x = __ldcg(p + v);
+        row[4 * v] = x.x & kIdBits; row[4 * v + 1] = x.y & kIdBits;
+        row[4 * v + 2] = x.z & kIdBits; row[4 * v + 3] = x.w & kIdBits;
+    }
+}
+
+// The same, marks kept (letter-masked rounds).
+template <int SS, int NB>
+static __device__ __forceinline__ void load_row_prefix_marked(const int32_t* sig, int s,
+                                                              int (&row)[SS])
+{
+    const int4* p = reinterpret_cast<const int4*>(sig + (int64_t)s * SS);
+#pragma unroll
+    for (int v = 0; v < NB; ++v) {
+        const int4 x = __ldcg(p + v);
         row[4 * v] = x.x; row[4 * v + 1] = x.y; row[4 * v + 2] = x.z; row[4 * v + 3] = x.w;
     }
+}
+
+// A leader's row as its members read it: only the first NB int4 (the successor ids; the head
+// and the padding are read from movers' rows only), so a leader stores just those.
+template <int SS, int NB>
+static __device__ __forceinline__ void store_row_prefix(int32_t* sig, int s, const int (&row)[SS])
+{
+    int4* p = reinterpret_cast<int4*>(sig + (int64_t)s * SS);
+#pragma unroll
+    for (int v = 0; v < NB; ++v)
+        __stcg(p + v, make_int4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]));
 }
 
 // Publish s's row (the table may point other states at it) before s enters a slot.
@@ -825,11 +862,45 @@ static __device__ bool stored_row_dirty(const Job& J, int s, int ncols, int pass
 // was a signature round) a leader whose stored row is still valid marks its block clean instead.
 template <int KC>
 static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, int ncols,
-                                     int pass, bool incr)
+                                     int pass, bool incr, bool masked)
 {
     const int gid = rank * (int)blockDim.x + (int)threadIdx.x, stride = T * (int)blockDim.x;
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
+        if constexpr (MaskOf<KC>::kFits) {
+            if (masked) {
+                // The stored row names the blocks X_a of the last round.  Entry a can change
+                // only if X_a lost members in that round (spl[X_a] == pass - 1); the others keep
+                // X_a, which is still the id of every state it held.  The row is rewritten with
+                // the entries that can change marked: members gather only those.
+                constexpr int NB = RowOf<KC>::NB;
+                for (int i = gid; i < nlead; i += stride) {
+                    const int s = __ldcg(&J.lead[i]);
+                    int row[SS], r[KC];
+                    load_row_prefix<SS, NB>(J.sig, s, row);
+                    load_succ<KC>(J.delta, s, r);
+                    unsigned mask = 0u;
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) {
+                        // an entry outside [0, n) cannot come from this launch's rounds: the
+                        // letter is gathered rather than trusted (and nothing is indexed by it)
+                        const int x = row[c];
+                        const bool chg = (unsigned)x >= (unsigned)J.n ||
+                                         __ldcg(&J.spl[x]) == pass - 1;
+                        mask |= (chg ? 1u : 0u) << c;
+                    }
+                    if (mask != 0u && !row_ok<KC>(J, r)) continue;
+#pragma unroll
+                    for (int c = 0; c < KC; ++c)
+                        if ((mask >> c) & 1u) row[c] = ld_blk(&J.block[r[c]]) | kChanged;
+                    row[KC] = s;
+#pragma unroll
+                    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                    store_row_prefix<SS, NB>(J.sig, s, row);
+                }
+                return;
+            }
+        }
         if (incr) {
             // U leaders per thread at a time, every load of a stage issued before any use: the
             // test is a chain of dependent reads (list, old row, spl, then delta and gathers)
@@ -849,8 +920,8 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
 #pragma unroll
                     for (int v = 0; v < NB; ++v) {
                         const int4 x = sv[u] >= 0 ? __ldcg(p + v) : make_int4(0, 0, 0, 0);
-                        old[u][4 * v] = x.x; old[u][4 * v + 1] = x.y;
-                        old[u][4 * v + 2] = x.z; old[u][4 * v + 3] = x.w;
+                        old[u][4 * v] = x.x & kIdBits; old[u][4 * v + 1] = x.y & kIdBits;
+                        old[u][4 * v + 2] = x.z & kIdBits; old[u][4 * v + 3] = x.w & kIdBits;
                     }
                 }
                 bool dirty[U];
@@ -877,7 +948,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                     row[KC] = sv[u];
 #pragma unroll
                     for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-                    store_row<SS>(J.sig, sv[u], row);
+                    store_row_prefix<SS, NB>(J.sig, sv[u], row);
                 }
             }
             return;
@@ -903,7 +974,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
             row[KC] = s;
 #pragma unroll
             for (int c = KC + 1; c < SS; ++c) row[c] = 0;
-            store_row<SS>(J.sig, s, row);
+            store_row_prefix<SS, RowOf<KC>::NB>(J.sig, s, row);
         }
     } else {
         const int nch = (ncols + 4) / 4;
@@ -998,15 +1069,89 @@ static __device__ __forceinline__ bool member_compare(const Job& J, int s, int L
     return member_decide<KC>(J, s, L, row, lr, slot);
 }
 
+// ---- phase B of a letter-masked round.  A member s of leader L had L's row in the last round,
+// so its entry for an unmarked letter is L's (the block it names kept every state); only the
+// marked letters are gathered and compared.  A member whose leader marked nothing keeps its
+// block after one row read.  Pipeline: the next state's leader row and the successors of the
+// state after it are in flight while the current state's marked letters are gathered.
+template <int KC>
+static __device__ void members_masked(const Job& J, int c0, int c1, int* s_cnt, int* s_heads)
+{
+    constexpr int SS = RowOf<KC>::SS;
+    constexpr int NB = RowOf<KC>::NB;
+    const int bd = (int)blockDim.x;
+    int L0 = -1, L1 = -1, r0[KC], r1[KC], lr0[SS];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) { r0[c] = 0; r1[c] = 0; }
+#pragma unroll
+    for (int c = 0; c < SS; ++c) lr0[c] = 0;
+    {
+        const int s = c0 + (int)threadIdx.x;
+        if (s < c1) { L0 = ld_blk(&J.block[s]); load_succ<KC>(J.delta, s, r0); }
+        if (s + bd < c1) { L1 = ld_blk(&J.block[s + bd]); load_succ<KC>(J.delta, s + bd, r1); }
+        if (s < c1 && L0 != s) load_row_prefix_marked<SS, NB>(J.sig, L0, lr0);
+    }
+    for (int base = c0; base < c1; base += bd) {
+        const int s = base + (int)threadIdx.x;
+        // issue the next state's leader row and the state after it
+        int lr1[SS];
+#pragma unroll
+        for (int c = 0; c < SS; ++c) lr1[c] = 0;
+        if (s + bd < c1 && L1 != s + bd) load_row_prefix_marked<SS, NB>(J.sig, L1, lr1);
+        int L2 = -1, r2[KC];
+#pragma unroll
+        for (int c = 0; c < KC; ++c) r2[c] = 0;
+        if (s + 2 * bd < c1) { L2 = ld_blk(&J.block[s + 2 * bd]); load_succ<KC>(J.delta, s + 2 * bd, r2); }
+
+        bool moved = false;
+        uint32_t slot = 0;
+        count_heads(s < c1 && L0 == s, s_heads);
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) any |= lr0[c] < 0;          // bit 31: marked
+        if (s < c1 && L0 != s && any && row_ok<KC>(J, r0)) {
+            int row[SS];
+            bool same = true;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                const int id = lr0[c] & kIdBits;
+                row[c] = lr0[c] < 0 ? ld_blk(&J.block[r0[c]]) : id;
+                same &= row[c] == id;
+            }
+            if (!same) {
+                row[KC] = L0;
+#pragma unroll
+                for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                uint64_t h = hash_begin(L0);
+#pragma unroll
+                for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
+                h = hash_final(h, L0, J.flags);
+                store_row<SS>(J.sig, s, row);
+                slot = (uint32_t)h & J.mask;
+                moved = true;
+            }
+        }
+        append_moved(J, c0, moved, s, slot, s_cnt);
+        L0 = L1;
+        L1 = L2;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) { r0[c] = r1[c]; r1[c] = r2[c]; }
+#pragma unroll
+        for (int c = 0; c < SS; ++c) lr0[c] = lr1[c];
+    }
+}
+
 // ---- phase B: members compare with their leader; those that differ are regrouped.
 // The loop is uniform across the CTA so that appends can be aggregated per warp.
 template <int KC>
 static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, int* s_claims, int* s_cnt,
-                              int* s_heads, int pass, bool incr)
+                              int* s_heads, int pass, bool incr, bool masked)
 {
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
-        if (incr) {
+        if (masked) {
+            if constexpr (MaskOf<KC>::kFits) members_masked<KC>(J, c0, c1, s_cnt, s_heads);
+        } else if (incr) {
             // 1. list the members of blocks that may split (their leader is not marked clean)
             //    in this CTA's segment of stg (states) and lst_rst (leaders).  Pipeline: the
             //    block id of the state after next and the clean mark of the next state's leader
@@ -1739,7 +1884,24 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             // the last round mark their old blocks, and a block is revisited when its row names
             // one of them, so with M movers and ncols columns about ncols * 2M / n of the blocks
             // are revisited.  Below a quarter of that bound the round is incremental.
-            const bool incr = have_rows && !leader_mode && !(J.flags & DFAMIN_FLAG_FULL_ROUNDS) &&
+            // a letter-masked round (rows of 8 ints or with room for the mask) reads one leader
+            // row per member and gathers only the letters whose block split; it replaces the
+            // incremental round and, while members outnumber leaders, the full one (a leader
+            // pays one row read and k split marks more, a member saves the unmarked gathers).
+            // With few blocks the per-CTA caches serve the leader rows instead.
+            const int nlead_round = ld_volatile(&J.ctrl->nlead);
+            bool masked = false;
+            if constexpr (MaskOf<KC>::kFits) {
+                masked = have_rows && !leader_mode &&
+                         !(J.flags & (DFAMIN_FLAG_FULL_ROUNDS | DFAMIN_FLAG_INCREMENTAL_ROUNDS)) &&
+                         ((J.flags & DFAMIN_FLAG_MASKED_ROUNDS) ||
+                          (count > kCacheMaxBlocks &&
+                           (2ll * nlead_round <= (long long)n ||
+                            moved_last * 4ull * (unsigned long long)max(ncols, 1) <=
+                                (unsigned long long)n)));
+            }
+            const bool incr = !masked && have_rows && !leader_mode &&
+                              !(J.flags & DFAMIN_FLAG_FULL_ROUNDS) &&
                               ((J.flags & DFAMIN_FLAG_INCREMENTAL_ROUNDS) ||
                                moved_last * 4ull * (unsigned long long)max(ncols, 1) <=
                                    (unsigned long long)n);
@@ -1753,7 +1915,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     else J.table[__ldcg(&J.lead_slot[i])] = kEmptySlot;
                 }
                 lead_reset_from = nlead;
-                phase_leaders<KC>(J, rank, T, nlead, ncols, passes, incr);
+                phase_leaders<KC>(J, rank, T, nlead, ncols, passes, incr, masked);
             }
             __syncthreads();
             if (threadIdx.x == 0) { s_claims = 0; s_cnt = 0; s_rst = 0; s_heads = 0; }
@@ -1765,7 +1927,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             if constexpr (KC > 0) {
                 extern __shared__ __align__(16) unsigned char dsm[];
                 auto& cache = *reinterpret_cast<CtaCache<RowOf<KC>::SS>*>(dsm);
-                use_cache = !leader_mode && count <= kCacheMaxBlocks;
+                use_cache = !leader_mode && !masked && count <= kCacheMaxBlocks;
                 if (use_cache) {
                     cache_clear(cache);
                     __syncthreads();
@@ -1773,10 +1935,11 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                              passes, incr);
                 } else {
                     phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads, passes,
-                                      incr);
+                                      incr, masked);
                 }
             } else {
-                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads, passes, incr);
+                phase_members<KC>(J, c0, c1, ncols, &s_claims, &s_cnt, &s_heads, passes, incr,
+                                  masked);
             }
             __syncthreads();
             {

@@ -27,6 +27,7 @@ FLAG_TRACE = 8
 FLAG_FULL_ROUNDS = 16
 FLAG_INCREMENTAL_ROUNDS = 32
 FLAG_BATCH_FOUR_CTAS = 64
+FLAG_MASKED_ROUNDS = 128
 TRACE_BYTES = 262144
 TRACE_PHASES = {0: "start", 1: "validate", 2: "init", 3: "closure", 4: "leaders",
                 5: "members", 6: "moves", 7: "count", 8: "canonical"}

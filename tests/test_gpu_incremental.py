@@ -1,11 +1,14 @@
-"""Incremental signature rounds and the bounded device waits, on the GPU through the C ABI.
+"""Incremental and letter-masked signature rounds and the bounded device waits, on the GPU
+through the C ABI.
 
 * A signature round after another one in which few states moved skips the blocks that cannot
-  split (their leader's row names no block that split in the round before).  Every case here
-  runs three ways, with the default choice, with DFAMIN_FLAG_FULL_ROUNDS and with
-  DFAMIN_FLAG_INCREMENTAL_ROUNDS (incremental whenever possible), and each must equal the
-  oracle element by element (partition, block count and pass count): skipping a block never
-  changes the result of Alg. sortPR's round.
+  split (their leader's row names no block that split in the round before); a letter-masked
+  round gathers, for each member, only the letters whose entry in its leader's row names a block
+  that split.  Every case here runs four ways, with the default choice, with
+  DFAMIN_FLAG_FULL_ROUNDS, with DFAMIN_FLAG_INCREMENTAL_ROUNDS (incremental whenever possible)
+  and with DFAMIN_FLAG_MASKED_ROUNDS (masked whenever the alphabet is compiled in), and each
+  must equal the oracle element by element (partition, block count and pass count): neither
+  skipping a block nor trusting an unchanged entry changes the result of Alg. sortPR's round.
 * Every wait of a CTA for its team is bounded.  A test-only bound of a microsecond makes a
   multi-CTA call end with DFAMIN_ETIMEOUT (no fault, no hang); the next call on the same
   context must be exact again.
@@ -41,9 +44,13 @@ def _run(dm, d, **kw):
     return dm.minimize_ex(d.n, d.k, dlt, acc, opt=dm.options(**kw)).host()
 
 
+def WAYS(dm):
+    return (0, dm.FLAG_FULL_ROUNDS, dm.FLAG_INCREMENTAL_ROUNDS, dm.FLAG_MASKED_ROUNDS)
+
+
 def both_ways(dm, d, closure=False, flags=0, **kw):
     want, wn, wp = _oracle(d, closure)
-    for extra in (0, dm.FLAG_FULL_ROUNDS, dm.FLAG_INCREMENTAL_ROUNDS):
+    for extra in WAYS(dm):
         got, gn, gp, st = _run(dm, d, closure=closure, flags=flags | extra, **kw)
         assert st == 0, dm.status_string(st)
         assert (gn, gp) == (wn, wp), (extra, gn, wn, gp, wp)
@@ -55,6 +62,10 @@ CASES = {
     "inflated_k3": lambda: I.inflated_dfa(30_000, 3, 4, 0.5, 2)[0],
     "inflated_k5_unpermuted": lambda: I.inflated_dfa(20_000, 5, 6, 0.5, 3, permute=False)[0],
     "inflated_k9": lambda: I.inflated_dfa(10_000, 9, 5, 0.5, 4)[0],
+    "inflated_k6": lambda: I.inflated_dfa(12_000, 6, 8, 0.5, 14)[0],
+    "inflated_k8": lambda: I.inflated_dfa(8_000, 8, 6, 0.3, 15)[0],
+    "inflated_k1": lambda: I.inflated_dfa(50_000, 1, 5, 0.5, 16)[0],
+    "inflated_k4_1e6": lambda: I.inflated_dfa(100_000, 4, 10, 0.5, 17)[0],
     "random_k2": lambda: I.random_dfa(150_000, 2, 0.5, 5),
     "random_k7_skewed": lambda: I.random_dfa(60_000, 7, 0.1, 6),
     "bitsplitter_b13": lambda: I.bitsplitter_dfa(13),
@@ -90,12 +101,13 @@ def test_incremental_rounds_on_the_closure(dm, maker):
 
 def test_incremental_rounds_in_a_batch(dm):
     dfas = [I.inflated_dfa(6_000, 4, 10, 0.5, 11)[0], I.cyclic_fib_dfa(15),
-            I.random_dfa(40_000, 3, 0.5, 12), I.bitsplitter_dfa(12), I.random_dfa(900, 2, 0.5, 13)]
+            I.random_dfa(40_000, 3, 0.5, 12), I.bitsplitter_dfa(12), I.random_dfa(900, 2, 0.5, 13),
+            I.inflated_dfa(4_000, 6, 8, 0.5, 18)[0], I.inflated_dfa(9_000, 2, 7, 0.5, 19)[0]]
     delta, acc, state_off, ks = dm.pack_batch(dfas)
     dd = torch.from_numpy(delta).cuda()
     aa = torch.from_numpy(acc.view(np.int32)).cuda()
     outs = []
-    for flags in (0, dm.FLAG_FULL_ROUNDS, dm.FLAG_INCREMENTAL_ROUNDS):
+    for flags in WAYS(dm) + (dm.FLAG_MASKED_ROUNDS | dm.FLAG_BATCH_FOUR_CTAS,):
         plan = dm.BatchPlan(state_off, ks, dm.options(flags=flags, team_states=4096))
         out, per = plan.run(dd, aa)
         outs.append((out.cpu().numpy(), per.cpu().numpy()))
