@@ -454,14 +454,15 @@ __device__ __forceinline__ bool row_ok(const Job& J, const int (&r)[KC])
     return ok;
 }
 
-// Row layout of the compile-time-width kernels: the successors' block ids first, then the head
-// (the state's own block id), zero padding to SS ints:  [b_0 .. b_{KC-1}, head, 0 ..].  A member
-// compares its successors' ids with its leader's (the heads are equal by definition), which
-// reads only the first NB int4 of the leader's row: one 16-byte load for KC <= 4.
+// Row layout of the compile-time-width kernels: the successors' block ids, zero padding to a
+// whole number of int4:  [b_0 .. b_{KC-1}, 0 ..], SS = 4 * NB ints (one 16-byte access for
+// KC <= 4).  The state's own block id (the head of its signature) is not in the row: a member
+// has its leader's head by definition, and movers are grouped under their old block id, which
+// the group-table slot holds beside the group's smallest state.
 template <int KC>
 struct RowOf {
-    static constexpr int SS = (KC + 1 + 3) / 4 * 4;
     static constexpr int NB = (KC + 3) / 4;
+    static constexpr int SS = 4 * NB;
 };
 
 // Letter-masked rounds mark, in a leader's row, the entries that can change this round: bit 31
@@ -501,8 +502,7 @@ static __device__ __forceinline__ void load_row_prefix_marked(const int32_t* sig
     }
 }
 
-// A leader's row as its members read it: only the first NB int4 (the successor ids; the head
-// and the padding are read from movers' rows only), so a leader stores just those.
+// The first NB int4 of a row (with SS = 4 * NB, the whole row).
 template <int SS, int NB>
 static __device__ __forceinline__ void store_row_prefix(int32_t* sig, int s, const int (&row)[SS])
 {
@@ -520,34 +520,47 @@ static __device__ __forceinline__ void publish_row(const Job& J, int s, const in
     __threadfence();
 }
 
-// Insert s into the table; returns the slot of s's group.  A slot is claimed by CAS from empty
-// by a state that published its row first (the representative); a member whose full row equals
-// the representative's lowers the slot's smallest member by atomicMin.  Ordinary members write
-// nothing.  Equality is decided on the full rows, never on the hash.
-template <int SS>
-static __device__ uint32_t insert_row(const Job& J, int s, uint64_t h, const int (&row)[SS],
-                               int* s_claims, bool published = false)
+// Compile-time-width group slots hold (smallest member << 32) | head, the head being the old
+// block id every member of the group shares.
+static __device__ __forceinline__ int slot_head(unsigned long long w) { return (int)(uint32_t)w; }
+
+// Insert s (old block id `head`, successor ids `row`) into the table; returns the slot of s's
+// group.  A slot is claimed by CAS from empty; a state whose head and row equal the group's
+// lowers the slot's smallest member by atomicMin.  A state publishes its row before it can
+// become a slot's smallest member (the claim or the atomicMin), so that the row of the member a
+// slot names is always readable: equality is decided on the head and the full row of that
+// member, never on the hash.  Other states write nothing.
+template <int KC>
+static __device__ uint32_t insert_row(const Job& J, int s, int head, uint64_t h,
+                                      const int (&row)[RowOf<KC>::SS], int* s_claims,
+                                      bool published = false)
 {
+    constexpr int SS = RowOf<KC>::SS;
     uint32_t idx = (uint32_t)h & J.mask;
     for (uint32_t probe = 0; probe <= J.mask; ++probe) {
         unsigned long long w = ld_acquire_u64(&J.table[idx]);
         if (w == kEmptySlot) {
             if (!published) { publish_row<SS>(J, s, row); published = true; }
-            w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, s));
+            w = atomicCAS(&J.table[idx], kEmptySlot, slot_word(s, head));
             if (w == kEmptySlot) {
                 atomicAdd(s_claims, 1);
                 return idx;
             }
-            __threadfence();   // acquire: the representative's row was published before its CAS
+            __threadfence();   // acquire: the named member's row was published before its atomic
         }
-        int tr[SS];
-        load_row<SS>(J.sig, slot_rep(w), tr);
-        bool eq = true;
+        if (slot_head(w) == head) {
+            int tr[SS];
+            load_row<SS>(J.sig, slot_min(w), tr);
+            bool eq = true;
 #pragma unroll
-        for (int c = 0; c < SS; ++c) eq &= (tr[c] == row[c]);
-        if (eq) {
-            if (s < slot_min(w)) atomicMin(&J.table[idx], slot_word(s, slot_rep(w)));
-            return idx;
+            for (int c = 0; c < KC; ++c) eq &= (tr[c] == row[c]);
+            if (eq) {
+                if (s < slot_min(w)) {
+                    if (!published) { publish_row<SS>(J, s, row); published = true; }
+                    atomicMin(&J.table[idx], slot_word(s, head));
+                }
+                return idx;
+            }
         }
         idx = (idx + 1) & J.mask;
     }
@@ -694,6 +707,7 @@ struct CtaCache {
     unsigned long long key[kSlots];
     uint32_t gslot[kSlots];              // kEmpty = entry unused
     int gmin[kSlots];
+    int head[kSlots];                    // the group's old block id
     int row[kSlots][SS];
     int lkey[kLeaderCache];
     int lcln[kLeaderCache];              // the leader's clean mark (incremental rounds)
@@ -777,9 +791,8 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
         if (visit && row_ok<KC>(J, r)) {
 #pragma unroll
             for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
-            row[KC] = L;
 #pragma unroll
-            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+            for (int c = KC; c < SS; ++c) row[c] = 0;
             bool same = true;
 #pragma unroll
             for (int c = 0; c < KC; ++c) same &= (row[c] == lr[c]);
@@ -790,16 +803,16 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
                 h = hash_final(h, L, J.flags);
                 const int ci = (int)(h & (uint64_t)(kSlots - 1));
                 bool hit = false;
-                if (C.gslot[ci] != kEmpty && C.key[ci] == h) {
+                if (C.gslot[ci] != kEmpty && C.key[ci] == h && C.head[ci] == L) {
                     hit = true;
 #pragma unroll
-                    for (int c = 0; c < SS; ++c) hit &= (C.row[ci][c] == row[c]);
+                    for (int c = 0; c < KC; ++c) hit &= (C.row[ci][c] == row[c]);
                 }
                 if (hit) {
                     slot = kCached | (uint32_t)ci;
                     moved = true;
                 } else {
-                    slot = insert_row<SS>(J, s, h, row, s_claims);
+                    slot = insert_row<KC>(J, s, L, h, row, s_claims);
                     moved = fill = slot != kFail;
                 }
             }
@@ -810,6 +823,7 @@ static __device__ void phase_members_cached(const Job& J, int c0, int c1, int* s
             const int ci = (int)(h & (uint64_t)(kSlots - 1));
             if (atomicCAS(&C.gslot[ci], kEmpty, slot) == kEmpty) {
                 C.key[ci] = h;
+                C.head[ci] = L;
 #pragma unroll
                 for (int c = 0; c < SS; ++c) C.row[ci][c] = row[c];
             }
@@ -893,9 +907,8 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
 #pragma unroll
                     for (int c = 0; c < KC; ++c)
                         if ((mask >> c) & 1u) row[c] = ld_blk(&J.block[r[c]]) | kChanged;
-                    row[KC] = s;
 #pragma unroll
-                    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                    for (int c = KC; c < SS; ++c) row[c] = 0;
                     store_row_prefix<SS, NB>(J.sig, s, row);
                 }
                 return;
@@ -930,7 +943,9 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                     dirty[u] = false;
                     if (sv[u] < 0) continue;
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) dirty[u] |= __ldcg(&J.spl[old[u][c]]) == pass - 1;
+                    for (int c = 0; c < KC; ++c)
+                        dirty[u] |= (unsigned)old[u][c] >= (unsigned)J.n ||
+                                    __ldcg(&J.spl[old[u][c]]) == pass - 1;
                 }
                 int r[U][KC];
 #pragma unroll
@@ -945,9 +960,8 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                     int row[SS];
 #pragma unroll
                     for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[u][c]]);
-                    row[KC] = sv[u];
 #pragma unroll
-                    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                    for (int c = KC; c < SS; ++c) row[c] = 0;
                     store_row_prefix<SS, NB>(J.sig, sv[u], row);
                 }
             }
@@ -971,9 +985,8 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
             int row[SS];
 #pragma unroll
             for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
-            row[KC] = s;
 #pragma unroll
-            for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+            for (int c = KC; c < SS; ++c) row[c] = 0;
             store_row_prefix<SS, RowOf<KC>::NB>(J.sig, s, row);
         }
     } else {
@@ -1028,9 +1041,8 @@ static __device__ __forceinline__ void member_row(const Job& J, int L, const int
     load_row_prefix<SS, RowOf<KC>::NB>(J.sig, L, lr);
 #pragma unroll
     for (int c = 0; c < KC; ++c) row[c] = ld_blk(&J.block[r[c]]);
-    row[KC] = L;
 #pragma unroll
-    for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+    for (int c = KC; c < SS; ++c) row[c] = 0;
 }
 
 template <int KC>
@@ -1119,9 +1131,8 @@ static __device__ void members_masked(const Job& J, int c0, int c1, int* s_cnt, 
                 same &= row[c] == id;
             }
             if (!same) {
-                row[KC] = L0;
 #pragma unroll
-                for (int c = KC + 1; c < SS; ++c) row[c] = 0;
+                for (int c = KC; c < SS; ++c) row[c] = 0;
                 uint64_t h = hash_begin(L0);
 #pragma unroll
                 for (int c = 0; c < KC; ++c) h = hash_step(h, row[c]);
@@ -1266,7 +1277,8 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
                 const uint32_t idx = __ldcg(&J.lst_slot[c0 + i]);
                 int row[SS];
                 load_row<SS>(J.sig, s, row);
-                const uint32_t slot = insert_row<SS>(J, s, (uint64_t)idx, row, s_claims, true);
+                const int head = ld_blk(&J.block[s]);   // s's old block (rewritten in phase C)
+                const uint32_t slot = insert_row<KC>(J, s, head, (uint64_t)idx, row, s_claims, true);
                 J.lst_slot[c0 + i] = slot;
             }
         }
@@ -1373,25 +1385,6 @@ static __device__ __forceinline__ void append_pair(const Job& J, int c0, int* cn
         const int pos = c0 + pos0 + __popc(m & ((1u << lane) - 1u));
         J.stg[pos] = s;
         J.lst_rst[pos] = slot;
-    }
-}
-
-// Phase C, for a mover s that leads its new group (signature rounds): the block s left lost
-// members this round (spl), and s's row must be in sig[] for the next round's incremental test.
-// Uncached members stored their rows already; a group entered through the CTA cache holds only
-// its representative's row, which equals s's (full-row equality), so it is copied.
-template <int SS>
-static __device__ __forceinline__ void new_leader_bookkeeping(const Job& J, int s, uint32_t gslot,
-                                                              int pass, bool cached_round)
-{
-    J.spl[__ldcg(&J.block[s])] = pass;                // before block[s] is overwritten
-    if (cached_round) {
-        const int rep = slot_rep(__ldcg(&J.table[gslot]));
-        if (rep != s) {
-            int row[SS];
-            load_row<SS>(J.sig, rep, row);
-            store_row<SS>(J.sig, s, row);
-        }
     }
 }
 
@@ -1993,26 +1986,31 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                                 slv[u] = __ldcs(&J.lst_slot[c0 + i]);
                             }
                         }
-                        int mv[4];
+                        int mv[4], hv[4];
                         uint32_t gsv[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             mv[u] = 0;
+                            hv[u] = 0;
                             gsv[u] = slv[u];
                             if (sv[u] < 0) continue;
                             if (use_cache && (slv[u] & kCached)) {
                                 const int ci = (int)(slv[u] & ~kCached);
                                 mv[u] = cache.gmin[ci];
+                                hv[u] = cache.head[ci];
                                 gsv[u] = cache.gslot[ci];
+                            } else if (leader_mode) {
+                                mv[u] = ld_volatile(&J.naive_new[slv[u]]);
                             } else {
-                                mv[u] = leader_mode ? ld_volatile(&J.naive_new[slv[u]])
-                                                    : slot_min(__ldcg(&J.table[slv[u]]));
+                                const unsigned long long w = __ldcg(&J.table[slv[u]]);
+                                mv[u] = slot_min(w);
+                                hv[u] = slot_head(w);
                             }
                         }
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            if (sv[u] >= 0 && mv[u] == sv[u] && !leader_mode)
-                                new_leader_bookkeeping<SS>(J, sv[u], gsv[u], passes, use_cache);
+                            // a new block: the block its smallest member left lost members
+                            if (sv[u] >= 0 && mv[u] == sv[u] && !leader_mode) J.spl[hv[u]] = passes;
                             if (sv[u] >= 0) J.block[sv[u]] = mv[u];
                             append_pair(J, c0, &s_rst, sv[u] >= 0 && mv[u] == sv[u], sv[u],
                                         gsv[u]);
