@@ -227,7 +227,17 @@ struct TeamSync {
     int64_t timeout_ns;
 };
 
-static __device__ __forceinline__ bool team_barrier(TeamSync& ts)
+// The control words a round reads after a barrier, fetched once per CTA (by the thread that
+// waited) instead of by every thread: all warps of all CTAs reading one word right after a
+// barrier queue thousands of requests at one L2 slice.
+struct CtrlSnap {
+    unsigned long long claims;
+    unsigned long long moved;
+    int nlead;
+};
+
+static __device__ __forceinline__ bool team_barrier(TeamSync& ts, const Ctrl* src = nullptr,
+                                                    CtrlSnap* snap = nullptr)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -258,6 +268,11 @@ static __device__ __forceinline__ bool team_barrier(TeamSync& ts)
         __threadfence();
         if (ld_volatile(ts.status) != 0) ok = 0;
         s_ok = ok;
+        if (snap) {
+            snap->claims = ld_acquire_u64(&src->claims);
+            snap->moved = ld_acquire_u64(&src->moved);
+            snap->nlead = ld_volatile(&src->nlead);
+        }
     }
     __syncthreads();
     return s_ok != 0;
@@ -887,29 +902,86 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                 // only if X_a lost members in that round (spl[X_a] == pass - 1); the others keep
                 // X_a, which is still the id of every state it held.  The row is rewritten with
                 // the entries that can change marked: members gather only those.
+                // U leaders per thread at a time, every load of a stage issued before any use:
+                // the test is a chain of dependent reads (list, old row, split marks, then the
+                // successors and the gathers of the marked letters).  A row without marks that
+                // needs none is left as it is.
                 constexpr int NB = RowOf<KC>::NB;
-                for (int i = gid; i < nlead; i += stride) {
-                    const int s = __ldcg(&J.lead[i]);
-                    int row[SS], r[KC];
-                    load_row_prefix<SS, NB>(J.sig, s, row);
-                    load_succ<KC>(J.delta, s, r);
-                    unsigned mask = 0u;
+                constexpr int U = KC <= 2 ? 2 : 1;
+                for (int i0 = gid; i0 < nlead; i0 += U * stride) {
+                    int sv[U];
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) {
-                        // an entry outside [0, n) cannot come from this launch's rounds: the
-                        // letter is gathered rather than trusted (and nothing is indexed by it)
-                        const int x = row[c];
-                        const bool chg = (unsigned)x >= (unsigned)J.n ||
-                                         __ldcg(&J.spl[x]) == pass - 1;
-                        mask |= (chg ? 1u : 0u) << c;
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * stride;
+                        sv[u] = i < nlead ? __ldcg(&J.lead[i]) : -1;
                     }
-                    if (mask != 0u && !row_ok<KC>(J, r)) continue;
+                    int row[U][SS];
 #pragma unroll
-                    for (int c = 0; c < KC; ++c)
-                        if ((mask >> c) & 1u) row[c] = ld_blk(&J.block[r[c]]) | kChanged;
+                    for (int u = 0; u < U; ++u) {
+                        if (sv[u] >= 0) {
+                            load_row_prefix_marked<SS, NB>(J.sig, sv[u], row[u]);
+                        } else {
 #pragma unroll
-                    for (int c = KC; c < SS; ++c) row[c] = 0;
-                    store_row_prefix<SS, NB>(J.sig, s, row);
+                            for (int c = 0; c < SS; ++c) row[u][c] = 0;
+                        }
+                    }
+                    // one leader per thread (wide rows): its successors are read with its row,
+                    // before the marks are known, to shorten the chain
+                    int r[U][KC];
+                    if constexpr (U == 1) {
+                        if (sv[0] >= 0) {
+                            load_succ<KC>(J.delta, sv[0], r[0]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) r[0][c] = 0;
+                        }
+                    }
+                    unsigned mask[U];
+                    bool had[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        mask[u] = 0u;
+                        had[u] = false;
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            had[u] |= row[u][c] < 0;
+                            const int x = row[u][c] & kIdBits;
+                            row[u][c] = x;
+                            // an entry outside [0, n) cannot come from this launch's rounds:
+                            // the letter is gathered rather than trusted (nothing indexed by it)
+                            const bool chg = sv[u] >= 0 && ((unsigned)x >= (unsigned)J.n ||
+                                                            __ldcg(&J.spl[x]) == pass - 1);
+                            mask[u] |= (chg ? 1u : 0u) << c;
+                        }
+                    }
+                    if constexpr (U > 1) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (mask[u] != 0u) {
+                                load_succ<KC>(J.delta, sv[u], r[u]);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < KC; ++c) r[u][c] = 0;
+                            }
+                        }
+                    }
+                    bool put[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        put[u] = sv[u] >= 0 && (mask[u] != 0u || had[u]);
+                        if (mask[u] != 0u && !row_ok<KC>(J, r[u])) put[u] = false;
+                        if (!put[u]) continue;
+#pragma unroll
+                        for (int c = 0; c < KC; ++c)
+                            if ((mask[u] >> c) & 1u) row[u][c] = ld_blk(&J.block[r[u][c]]) | kChanged;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!put[u]) continue;
+#pragma unroll
+                        for (int c = KC; c < SS; ++c) row[u][c] = 0;
+                        store_row_prefix<SS, NB>(J.sig, sv[u], row[u]);
+                    }
                 }
                 return;
             }
@@ -1867,6 +1939,8 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
         // (not after the pattern, dense-code or key rounds)
         bool have_rows = false;
         unsigned long long moved_seen = 0, moved_last = 0;
+        __shared__ CtrlSnap s_snap;
+        int nlead_cur = ld_volatile(&J.ctrl->nlead);      // leaders listed for the next round
         while (!stable1 && (leader_mode || count < n)) {
             if (passes >= max_passes) {
                 set_status(J.ctrl, DFAMIN_ENOCONVERGE);
@@ -1882,7 +1956,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             // incremental round and, while members outnumber leaders, the full one (a leader
             // pays one row read and k split marks more, a member saves the unmarked gathers).
             // With few blocks the per-CTA caches serve the leader rows instead.
-            const int nlead_round = ld_volatile(&J.ctrl->nlead);
+            const int nlead_round = nlead_cur;
             bool masked = false;
             if constexpr (MaskOf<KC>::kFits) {
                 masked = have_rows && !leader_mode &&
@@ -1901,7 +1975,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             // ---- phase A: empty the slots of last round's groups (listed in phase C by each
             //      group's smallest state), then leaders publish rows
             {
-                const int nlead = ld_volatile(&J.ctrl->nlead);
+                const int nlead = nlead_cur;
                 const int gid = rank * (int)blockDim.x + (int)threadIdx.x;
                 for (int i = lead_reset_from + gid; i < nlead; i += T * (int)blockDim.x) {
                     if (leader_mode) J.naive_new[__ldcg(&J.lead_slot[i])] = 0x7fffffff;
@@ -1942,13 +2016,13 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     atomicAdd(&J.ctrl->moved, (unsigned long long)s_cnt);
                 if (threadIdx.x == 0) J.cta_cnt[rank] = s_heads;
             }
-            if (!team_barrier(ts)) goto done;
+            if (!team_barrier(ts, J.ctrl, &s_snap)) goto done;
             trace_mark(J, tw, passes, 5);
 
-            const unsigned long long claims_now = ld_acquire_u64(&J.ctrl->claims);
+            const unsigned long long claims_now = s_snap.claims;
             const int new_groups = (int)(claims_now - claims_seen);
             claims_seen = claims_now;
-            const unsigned long long moved_now = ld_acquire_u64(&J.ctrl->moved);
+            const unsigned long long moved_now = s_snap.moved;
             moved_last = moved_now - moved_seen;
             moved_seen = moved_now;
             if (new_groups == 0) {                    // partition unchanged: stable
@@ -2046,9 +2120,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     J.lead_slot[lbase + i] = J.lst_rst[c0 + i];
                 }
             }
-            if (!team_barrier(ts)) goto done;
+            if (!team_barrier(ts, J.ctrl, &s_snap)) goto done;
             trace_mark(J, tw, passes, 6);
-            count = leader_mode ? ld_volatile(&J.ctrl->nlead) : count + new_groups;
+            nlead_cur = s_snap.nlead;
+            count = leader_mode ? nlead_cur : count + new_groups;
             have_rows = !leader_mode;
         }
         if (ld_volatile(&J.ctrl->status) != 0) goto done;

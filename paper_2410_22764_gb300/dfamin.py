@@ -424,23 +424,53 @@ def minimize_host(n: int, k: int, delta: np.ndarray, accept: np.ndarray, *,
 # ------------------------------------------------------------------------------------------
 # Batches
 # ------------------------------------------------------------------------------------------
-def pack_batch(dfas):
-    """Concatenate host DFAs (objects with n, k, delta, accept) into the batch layout of the C
-    ABI: (delta int32, accept uint32 bitmap over all states, state_off int64, k int32)."""
+def batch_offsets(dfas):
+    """(state_off int64[count + 1], k int32[count]) of host DFAs in batch order."""
     ns = np.array([d.n for d in dfas], dtype=np.int64)
     ks = np.array([d.k for d in dfas], dtype=np.int32)
     state_off = np.zeros(len(dfas) + 1, dtype=np.int64)
     state_off[1:] = np.cumsum(ns)
-    delta = np.concatenate([np.asarray(d.delta, dtype=np.int32).reshape(-1) for d in dfas]
-                           + [np.zeros(0, np.int32)])
-    bits = np.concatenate([np.unpackbits(np.ascontiguousarray(d.accept, dtype=np.uint32)
-                                         .view(np.uint8), bitorder="little")[: d.n]
-                           for d in dfas])
-    packed = np.packbits(bits, bitorder="little")
-    words = (bits.size + 31) // 32
-    buf = np.zeros(words * 4, dtype=np.uint8)
-    buf[: packed.size] = packed
-    return delta, buf.view("<u4").astype(np.uint32), state_off, ks
+    return state_off, ks
+
+
+def pack_batch(dfas, delta_out: np.ndarray | None = None, accept_out: np.ndarray | None = None):
+    """Concatenate host DFAs (objects with n, k, delta, accept) into the batch layout of the C
+    ABI: (delta int32, accept uint32 bitmap over all states, state_off int64, k int32).
+
+    delta_out / accept_out: optional preallocated arrays (for instance views of page-locked
+    tensors) of at least sum(n*k) int32 and ceil(sum(n) / 32) uint32, written in place (the
+    returned arrays are views of them).  Each DFA's acceptance words are shifted to its bit
+    offset in the batch bitmap word by word; bits beyond a DFA's n are cleared."""
+    state_off, ks = batch_offsets(dfas)
+    total = int(state_off[-1])
+    nd = int(sum(int(d.n) * int(d.k) for d in dfas))
+    words = (total + 31) // 32
+    delta = (np.empty(nd, dtype=np.int32) if delta_out is None
+             else delta_out.reshape(-1)[:nd].view(np.int32))
+    pos = 0
+    for d in dfas:
+        m = int(d.n) * int(d.k)
+        delta[pos: pos + m] = np.asarray(d.delta, dtype=np.int32).reshape(-1)[:m]
+        pos += m
+    acc64 = np.zeros(words + 1, dtype=np.uint64)
+    for d, off in zip(dfas, state_off[:-1]):
+        n = int(d.n)
+        if n == 0:
+            continue
+        nw = (n + 31) // 32
+        a = np.ascontiguousarray(d.accept, dtype=np.uint32).reshape(-1)[:nw].astype(np.uint64)
+        if n % 32:
+            a[-1] &= np.uint64((1 << (n % 32)) - 1)
+        w0, sh = divmod(int(off), 32)
+        v = a << np.uint64(sh)
+        acc64[w0: w0 + nw] |= v & np.uint64(0xFFFFFFFF)
+        acc64[w0 + 1: w0 + nw + 1] |= v >> np.uint64(32)
+    if accept_out is None:
+        accept = acc64[:words].astype(np.uint32)
+    else:
+        accept = accept_out.reshape(-1)[:words].view(np.uint32)
+        accept[:] = acc64[:words]
+    return delta, accept, state_off, ks
 
 
 class BatchPlan:

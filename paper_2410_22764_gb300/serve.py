@@ -188,7 +188,13 @@ class Server:
             r.attempts += 1
         nbytes = sum(r.nbytes for r in reqs)
         self.used += nbytes
-        delta, acc, state_off, ks = dfamin.pack_batch(reqs)
+        # pack straight into page-locked buffers (one host copy of the rows)
+        state_off, ks = dfamin.batch_offsets(reqs)
+        nd = int(sum(r.n * r.k for r in reqs))
+        words = (int(state_off[-1]) + 31) // 32
+        h_delta = torch.empty(max(nd, 1), dtype=torch.int32, pin_memory=True)
+        h_acc = torch.empty(max(words, 1), dtype=torch.int32, pin_memory=True)
+        delta, acc, state_off, ks = dfamin.pack_batch(reqs, h_delta.numpy(), h_acc.numpy())
         opt = dfamin.options(closure=closure, max_passes=0 if closure else self.pass_cap,
                              flags=self.flags)
         if self.tuned:
@@ -197,16 +203,14 @@ class Server:
                 opt.smem_states, opt.team_states, opt.ctas = t.smem_states, t.team_states, t.ctas
                 opt.flags |= t.flags
         plan = dfamin.BatchPlan(state_off, ks, opt)
-        h_delta = torch.from_numpy(delta).pin_memory()
-        h_acc = torch.from_numpy(acc.view(np.int32)).pin_memory()
         host_out = torch.empty(plan.states, dtype=torch.int32, pin_memory=True)
         host_per = torch.empty((3, plan.count), dtype=torch.int32, pin_memory=True)
         ev_start = torch.cuda.Event(enable_timing=True)
         ev_end = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(s):
             ev_start.record(s)
-            d_delta = torch.empty(delta.size, dtype=torch.int32, device=self.device)
-            d_acc = torch.empty(acc.size, dtype=torch.int32, device=self.device)
+            d_delta = torch.empty(h_delta.numel(), dtype=torch.int32, device=self.device)
+            d_acc = torch.empty(h_acc.numel(), dtype=torch.int32, device=self.device)
             d_delta.copy_(h_delta, non_blocking=True)
             d_acc.copy_(h_acc, non_blocking=True)
             ws = dfamin.Workspace(self.device)
