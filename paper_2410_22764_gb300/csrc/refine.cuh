@@ -1630,11 +1630,12 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             // round 2 by dense codes (below) needs only the patterns: then round 1's ids and
             // leader list, which it would overwrite, are not written
             constexpr int PB = KC + 1;
+            constexpr int CB = 1 + KC * PB;           // bits of a round-2 code (below)
             bool dense_next = false;
-            if constexpr (PB * PB <= 26) {
+            if constexpr (CB <= 26) {
                 const uint64_t words = 2ull * ((uint64_t)J.mask + 1);
                 dense_next = round1_count1 != round1_count0 && round1_count1 < n &&
-                             J.max_passes >= 2 && (1ull << (PB * PB)) <= words;
+                             J.max_passes >= 2 && (1ull << CB) <= words;
             }
             if (!dense_next) {
                 for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x)
@@ -1651,12 +1652,16 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             round1_done = true;
 
             // ---- round 2 by dense codes.  After round 1 a block is a (k+1)-bit pattern, so a
-            //      state's round-2 signature is exactly the code formed by the patterns of the
-            //      state and its successors ((k+1)^2 bits).  For k <= 4 the code indexes a
-            //      direct table (the group table's memory seen as 32-bit words, all ones = empty):
-            //      one atomicMin per state gives every group its smallest state, with no hashing
-            //      and no row comparison.  Same partition and pass count as the general round.
-            if constexpr (PB * PB <= 26) {
+            //      state's round-2 signature is exactly the patterns of the state and of its
+            //      successors.  The state's own pattern repeats the successors' acceptance bits,
+            //      which their patterns hold too, so the signature is exactly the code of the
+            //      state's acceptance and its successors' patterns: 1 + k(k+1) bits (21 for
+            //      k = 4).  For k <= 4 the code indexes a direct table (the group table's memory
+            //      seen as 32-bit words, all ones = empty; 8 MB for k = 4, so that the groups'
+            //      words stay in L2): one atomicMin per state gives every group its smallest
+            //      state, with no hashing and no row comparison.  Same partition and pass count
+            //      as the general round.
+            if constexpr (CB <= 26) {
                 if (dense_next) {
                     uint32_t* dtab = reinterpret_cast<uint32_t*>(J.table);
                     const int32_t* pidx = J.naive_new;
@@ -1686,10 +1691,10 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                             code[u] = 0;
                             if (qv[u] >= c1) continue;
                             const int (&r)[KC] = rr[u];
-                            code[u] = (uint32_t)__ldcs(&pidx[qv[u]]);
+                            code[u] = (uint32_t)__ldcs(&pidx[qv[u]]) & 1u;   // acceptance of q
 #pragma unroll
                             for (int c = 0; c < KC; ++c)
-                                code[u] = (code[u] << PB) | (uint32_t)ld_blk(&pidx[r[c]]);
+                                code[u] |= (uint32_t)ld_blk(&pidx[r[c]]) << (1 + c * PB);
                         }
                         uint32_t old[2] = {0u, 0u};
 #pragma unroll
