@@ -486,10 +486,6 @@ struct RowOf {
 constexpr int kChanged = (int)0x80000000u;
 constexpr int kIdBits = 0x7fffffff;
 
-template <int KC>
-struct MaskOf {
-    static constexpr bool kFits = KC > 0;
-};
 
 // The first NB int4 of a row: a leader's successor ids (marks cleared).
 template <int SS, int NB>
@@ -878,7 +874,10 @@ static __device__ bool stored_row_dirty(const Job& J, int s, int ncols, int pass
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = 4 * v + j;               // entry i is column i - 1
-            if (i >= 1 && i <= ncols) dirty |= __ldcg(&J.spl[e[j]]) == pass - 1;
+            if (i >= 1 && i <= ncols) {
+                const int x = e[j] & kIdBits;
+                dirty |= (unsigned)x >= (unsigned)J.n || __ldcg(&J.spl[x]) == pass - 1;
+            }
         }
     }
     J.cln[s] = dirty ? 0 : pass;
@@ -896,7 +895,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
     const int gid = rank * (int)blockDim.x + (int)threadIdx.x, stride = T * (int)blockDim.x;
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
-        if constexpr (MaskOf<KC>::kFits) {
+        {
             if (masked) {
                 // The stored row names the blocks X_a of the last round.  Entry a can change
                 // only if X_a lost members in that round (spl[X_a] == pass - 1); the others keep
@@ -1233,7 +1232,7 @@ static __device__ void phase_members(const Job& J, int c0, int c1, int ncols, in
     if constexpr (KC > 0) {
         constexpr int SS = RowOf<KC>::SS;
         if (masked) {
-            if constexpr (MaskOf<KC>::kFits) members_masked<KC>(J, c0, c1, s_cnt, s_heads);
+            members_masked<KC>(J, c0, c1, s_cnt, s_heads);
         } else if (incr) {
             // 1. list the members of blocks that may split (their leader is not marked clean)
             //    in this CTA's segment of stg (states) and lst_rst (leaders).  Pipeline: the
@@ -1962,16 +1961,15 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             // pays one row read and k split marks more, a member saves the unmarked gathers).
             // With few blocks the per-CTA caches serve the leader rows instead.
             const int nlead_round = nlead_cur;
-            bool masked = false;
-            if constexpr (MaskOf<KC>::kFits) {
-                masked = have_rows && !leader_mode &&
-                         !(J.flags & (DFAMIN_FLAG_FULL_ROUNDS | DFAMIN_FLAG_INCREMENTAL_ROUNDS)) &&
-                         ((J.flags & DFAMIN_FLAG_MASKED_ROUNDS) ||
-                          (count > kCacheMaxBlocks &&
-                           (2ll * nlead_round <= (long long)n ||
-                            moved_last * 4ull * (unsigned long long)max(ncols, 1) <=
-                                (unsigned long long)n)));
-            }
+            // (compile-time widths only: for the runtime width the extra code cost registers and
+            // the marks saved nothing on the bit-splitters and the batches' random DFAs)
+            const bool masked =
+                KC > 0 && have_rows && !leader_mode &&
+                !(J.flags & (DFAMIN_FLAG_FULL_ROUNDS | DFAMIN_FLAG_INCREMENTAL_ROUNDS)) &&
+                ((J.flags & DFAMIN_FLAG_MASKED_ROUNDS) ||
+                 (count > kCacheMaxBlocks &&
+                  (2ll * nlead_round <= (long long)n ||
+                   moved_last * 4ull * (unsigned long long)max(ncols, 1) <= (unsigned long long)n)));
             const bool incr = !masked && have_rows && !leader_mode &&
                               !(J.flags & DFAMIN_FLAG_FULL_ROUNDS) &&
                               ((J.flags & DFAMIN_FLAG_INCREMENTAL_ROUNDS) ||

@@ -2,10 +2,13 @@
 
 Requests (host DFAs) arrive at any time.  The scheduler admits them in arrival order while the
 device memory they need fits in an HBM budget, packs everything admitted since the last launch
-into one batch (one persistent launch, ``dfamin_batch_plan_run``) on a free stream, and keeps
-several batches in flight at once, so work of requests that arrived while others were running
-overlaps on the device.  Finished batches are found by polling their events; their results are
-copied back asynchronously and their memory returns to the budget.
+into one batch (one persistent launch, ``dfamin_batch_plan_run``), and keeps several batches in
+flight at once: a batch's host-to-device copies run on a copy stream while earlier batches
+compute, and the launches themselves run one after another on one compute stream.  (A batch
+launch fills the GPU with CTAs whose teams wait for one another; two such launches side by
+side can leave a team's CTAs unscheduled behind the other launch's waiting CTAs until the
+team's bounded wait runs out.)  Finished batches are found by polling their events; their
+results are copied back asynchronously and their memory returns to the budget.
 
 Deep-refinement requests are run first with a pass cap; those that hit it
 (``DFAMIN_ENOCONVERGE``) are rerun on the partial transitive closure (Alg. transPR, Sec. 3.4),
@@ -79,7 +82,7 @@ class Server:
     """Continuous-batching server.
 
     budget_bytes    device memory the requests in flight may hold together (admission bound)
-    streams         batches that may be in flight at once
+    streams         batches that may be in flight at once (copies overlap, launches do not)
     max_batch       requests per batch at most
     max_batch_work  transitions (sum of n*k) per batch at most, except that a batch always takes
                     at least one request: a small bound keeps short requests from waiting behind
@@ -94,8 +97,14 @@ class Server:
                  max_batch_work: int = 1 << 62, tuned: bool = True):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.copy_stream = torch.cuda.Stream(device=self.device)
+        self.compute_stream = torch.cuda.Stream(device=self.device)
         self.free = list(range(streams))
+        # page-locked staging per stream (rows, acceptance words, labels, per-DFA scalars),
+        # grown on demand and reused: a stream's buffers are free again once its batch's end
+        # event has been seen, and pinning fresh host memory for every batch costs more than
+        # the copy itself
+        self._staging = [dict() for _ in range(streams)]
         self.max_batch = max_batch
         self.max_batch_work = int(max_batch_work)
         self.pass_cap = pass_cap
@@ -181,7 +190,7 @@ class Server:
 
     def _launch(self, reqs, closure: bool):
         si = self.free.pop()
-        s = self.streams[si]
+        cs, s = self.copy_stream, self.compute_stream
         now = time.perf_counter()
         for r in reqs:
             r.admitted = now
@@ -192,8 +201,8 @@ class Server:
         state_off, ks = dfamin.batch_offsets(reqs)
         nd = int(sum(r.n * r.k for r in reqs))
         words = (int(state_off[-1]) + 31) // 32
-        h_delta = torch.empty(max(nd, 1), dtype=torch.int32, pin_memory=True)
-        h_acc = torch.empty(max(words, 1), dtype=torch.int32, pin_memory=True)
+        h_delta = self._stage(si, "delta", max(nd, 1))
+        h_acc = self._stage(si, "acc", max(words, 1))
         delta, acc, state_off, ks = dfamin.pack_batch(reqs, h_delta.numpy(), h_acc.numpy())
         opt = dfamin.options(closure=closure, max_passes=0 if closure else self.pass_cap,
                              flags=self.flags)
@@ -203,16 +212,23 @@ class Server:
                 opt.smem_states, opt.team_states, opt.ctas = t.smem_states, t.team_states, t.ctas
                 opt.flags |= t.flags
         plan = dfamin.BatchPlan(state_off, ks, opt)
-        host_out = torch.empty(plan.states, dtype=torch.int32, pin_memory=True)
-        host_per = torch.empty((3, plan.count), dtype=torch.int32, pin_memory=True)
+        host_out = self._stage(si, "out", plan.states)
+        host_per = self._stage(si, "per", 3 * plan.count).view(3, plan.count)
         ev_start = torch.cuda.Event(enable_timing=True)
+        ev_copied = torch.cuda.Event()
         ev_end = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(s):
-            ev_start.record(s)
+            # allocated on the compute stream and filled on the copy stream; a batch's device
+            # memory is released only after its end event has been seen (every use finished)
             d_delta = torch.empty(h_delta.numel(), dtype=torch.int32, device=self.device)
             d_acc = torch.empty(h_acc.numel(), dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(cs):
+            ev_start.record(cs)
             d_delta.copy_(h_delta, non_blocking=True)
             d_acc.copy_(h_acc, non_blocking=True)
+            ev_copied.record(cs)
+        s.wait_event(ev_copied)
+        with torch.cuda.stream(s):
             ws = dfamin.Workspace(self.device)
             out, per = plan.run(d_delta, d_acc, workspace=ws, stream=s)
             host_out.copy_(out, non_blocking=True)
@@ -223,6 +239,15 @@ class Server:
                                     state_off, ev_start, ev_end, nbytes))
         self.stats.batches += 1
         self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
+
+    def _stage(self, si: int, name: str, count: int) -> torch.Tensor:
+        """The first `count` int32 of stream si's page-locked buffer `name` (grown by doubling)."""
+        buf = self._staging[si].get(name)
+        if buf is None or buf.numel() < count:
+            size = max(count, 2 * buf.numel() if buf is not None else 0, 1 << 16)
+            buf = torch.empty(size, dtype=torch.int32, pin_memory=True)
+            self._staging[si][name] = buf
+        return buf[:count]
 
     def _finish(self, b: _Batch):
         now = time.perf_counter()

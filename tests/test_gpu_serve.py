@@ -1,5 +1,6 @@
 """The continuous-batching server: every result is identical alone and in the mix (bit-exact,
-as all outputs are integers) and equal to the oracle; batches overlap on the device; admission
+as all outputs are integers) and equal to the oracle; batches in flight overlap their copies
+with earlier launches (the launches run one after another); admission
 respects the HBM budget; cancellation and a bad request affect nobody else."""
 import time
 
@@ -102,7 +103,8 @@ def test_batches_overlap_on_device(mods):
     dfamin, serve = mods
     from oracle.path_depth import path_passes
     # plain deep-refinement requests (36,880 rounds each, long on the device, light on the
-    # host) launched one per tick: later batches start while earlier ones still run
+    # host) launched one per tick: later batches are in flight, their copies under way, while
+    # earlier ones still run (the launches themselves follow one another on one stream)
     d = I.path_fib_dfa(65536)
     srv = serve.Server(budget_bytes=64 << 30, streams=4, pass_cap=100_000)
     for _ in range(3):
