@@ -326,6 +326,9 @@ def main():
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-pool", type=int, default=256,
                     help="distinct DFAs the served stream draws its requests from")
+    ap.add_argument("--solo-work", type=int, default=None,
+                    help="served stream: requests with n*k at least this run as single-DFA "
+                         "launches (server default when omitted; 0 = never)")
     ap.add_argument("--max-batch-work", type=int, default=1 << 25,
                     help="served stream: transitions per batch at most")
     ap.add_argument("--path-variant", default="both", choices=["both", "closure", "plain"])

@@ -258,10 +258,11 @@ def _latency_stats(lat, t_elapsed, R, rate):
             "p99_ms": float(np.percentile(lat, 99) * 1e3)}
 
 
-def _serve_batched(reqs, rate, max_work):
+def _serve_batched(reqs, rate, max_work, solo_work=None):
     from paper_2410_22764_gb300 import serve
     R = len(reqs)
-    srv = serve.Server(budget_bytes=48 << 30, streams=4, max_batch_work=max_work)
+    kw = {} if solo_work is None else {"solo_work": solo_work}
+    srv = serve.Server(budget_bytes=48 << 30, streams=4, max_batch_work=max_work, **kw)
     rng = np.random.default_rng(11)
     gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
     t0 = time.perf_counter()
@@ -281,7 +282,7 @@ def _serve_batched(reqs, rate, max_work):
     out.update({"failed": sum(1 for r in srv.completed if r.status != 0),
                 "batches": srv.stats.batches, "max_inflight": srv.stats.max_inflight,
                 "max_device_overlap": srv.max_device_overlap(),
-                "escalated": srv.stats.escalated})
+                "escalated": srv.stats.escalated, "single_dfa_launches": srv.stats.solo})
     return out
 
 
@@ -332,18 +333,21 @@ def run_serve(args):
     pick = np.random.default_rng(7).integers(0, len(pool), size=R)
     reqs = [pool[int(i)] for i in pick]
     W = args.max_batch_work
-    _serve_batched(reqs[: min(R, 200)], 0, W)          # warm-up (allocator, plans, kernels)
-    sat = _serve_batched(reqs, 0, W)
+    S = getattr(args, "solo_work", None)
+    _serve_batched(reqs[: min(R, 200)], 0, W, S)       # warm-up (allocator, plans, kernels)
+    sat = _serve_batched(reqs, 0, W, S)
     batched = {"saturated": sat}
     plain_sat = _serve_plain(reqs, 0)
     plain = {"saturated": plain_sat}
     for rho in (0.5, 0.8, 0.95):
         rate = rho * sat["dfas_per_s"]
-        batched[f"rho_{rho}"] = _serve_batched(reqs, rate, W)
+        batched[f"rho_{rho}"] = _serve_batched(reqs, rate, W, S)
         plain[f"rho_{rho}"] = _serve_plain(reqs, rate)
     _line(f"served Poisson stream, {R} requests drawn from a pool of {len(pool)} DFAs (n "
           "log-uniform 1e3..4e6, k 2..8, 50% random / 50% inflated c=4, 5% path n=65536), HBM "
-          f"budget 48 GB, batches of at most {W} transitions", sat["dfas_per_s"], "DFAs/s",
+          f"budget 48 GB, batches of at most {W} transitions, requests of at least "
+          f"{S if S is not None else 'the default'} transitions as single-DFA launches",
+          sat["dfas_per_s"], "DFAs/s",
           1e3 / sat["dfas_per_s"], R, 1,
           {"serve": batched, "plain_one_launch_per_request": plain,
            "batched_vs_plain_saturated": sat["dfas_per_s"] / plain_sat["dfas_per_s"],

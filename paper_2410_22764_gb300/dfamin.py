@@ -433,25 +433,12 @@ def batch_offsets(dfas):
     return state_off, ks
 
 
-def pack_batch(dfas, delta_out: np.ndarray | None = None, accept_out: np.ndarray | None = None):
-    """Concatenate host DFAs (objects with n, k, delta, accept) into the batch layout of the C
-    ABI: (delta int32, accept uint32 bitmap over all states, state_off int64, k int32).
-
-    delta_out / accept_out: optional preallocated arrays (for instance views of page-locked
-    tensors) of at least sum(n*k) int32 and ceil(sum(n) / 32) uint32, written in place (the
-    returned arrays are views of them).  Each DFA's acceptance words are shifted to its bit
-    offset in the batch bitmap word by word; bits beyond a DFA's n are cleared."""
-    state_off, ks = batch_offsets(dfas)
+def pack_accept(dfas, state_off, accept_out: np.ndarray | None = None):
+    """The batch acceptance bitmap: DFA i's state q at bit state_off[i] + q.  Each DFA's words
+    are shifted to its bit offset word by word; bits beyond a DFA's n are cleared.  Written into
+    accept_out (at least ceil(sum(n) / 32) 32-bit words) when given."""
     total = int(state_off[-1])
-    nd = int(sum(int(d.n) * int(d.k) for d in dfas))
     words = (total + 31) // 32
-    delta = (np.empty(nd, dtype=np.int32) if delta_out is None
-             else delta_out.reshape(-1)[:nd].view(np.int32))
-    pos = 0
-    for d in dfas:
-        m = int(d.n) * int(d.k)
-        delta[pos: pos + m] = np.asarray(d.delta, dtype=np.int32).reshape(-1)[:m]
-        pos += m
     acc64 = np.zeros(words + 1, dtype=np.uint64)
     for d, off in zip(dfas, state_off[:-1]):
         n = int(d.n)
@@ -466,11 +453,41 @@ def pack_batch(dfas, delta_out: np.ndarray | None = None, accept_out: np.ndarray
         acc64[w0: w0 + nw] |= v & np.uint64(0xFFFFFFFF)
         acc64[w0 + 1: w0 + nw + 1] |= v >> np.uint64(32)
     if accept_out is None:
-        accept = acc64[:words].astype(np.uint32)
+        return acc64[:words].astype(np.uint32)
+    accept = accept_out.reshape(-1)[:words].view(np.uint32)
+    accept[:] = acc64[:words]
+    return accept
+
+
+def pack_batch(dfas, delta_out=None, accept_out: np.ndarray | None = None):
+    """Concatenate host DFAs (objects with n, k, delta, accept) into the batch layout of the C
+    ABI: (delta int32, accept uint32 bitmap over all states, state_off int64, k int32).
+
+    delta_out / accept_out: optional preallocated outputs (for instance page-locked memory) of
+    at least sum(n*k) int32 and ceil(sum(n) / 32) uint32, written in place.  delta_out may be a
+    numpy array or a CPU torch tensor (then the rows are copied by torch, in parallel over the
+    host's cores, and a numpy view of it is returned)."""
+    state_off, ks = batch_offsets(dfas)
+    nd = int(sum(int(d.n) * int(d.k) for d in dfas))
+    if isinstance(delta_out, torch.Tensor):
+        flat = delta_out.reshape(-1)[:nd]
+        pos = 0
+        for d in dfas:
+            m = int(d.n) * int(d.k)
+            if m:
+                src = np.ascontiguousarray(d.delta, dtype=np.int32).reshape(-1)[:m]
+                flat[pos: pos + m].copy_(torch.from_numpy(src))
+            pos += m
+        delta = flat.numpy()
     else:
-        accept = accept_out.reshape(-1)[:words].view(np.uint32)
-        accept[:] = acc64[:words]
-    return delta, accept, state_off, ks
+        delta = (np.empty(nd, dtype=np.int32) if delta_out is None
+                 else delta_out.reshape(-1)[:nd].view(np.int32))
+        pos = 0
+        for d in dfas:
+            m = int(d.n) * int(d.k)
+            delta[pos: pos + m] = np.asarray(d.delta, dtype=np.int32).reshape(-1)[:m]
+            pos += m
+    return delta, pack_accept(dfas, state_off, accept_out), state_off, ks
 
 
 class BatchPlan:

@@ -75,6 +75,7 @@ class ServerStats:
     max_inflight: int = 0
     escalated: int = 0
     rejected: int = 0
+    solo: int = 0                                   # requests run as single-DFA launches
     intervals: list = field(default_factory=list)   # (start_ms, end_ms) of every batch on device
 
 
@@ -88,13 +89,19 @@ class Server:
                     at least one request: a small bound keeps short requests from waiting behind
                     one huge batch, and lets more batches overlap on the device
     pass_cap        plain-refinement passes before a request is rerun on the closure
+    solo_work       transitions (n*k) from which a request runs as its own single-DFA launch
+                    (`dfamin_minimize_ex`, the whole GPU for one DFA) instead of joining a
+                    batch, in which it would get one team and hold the batch up; 0 = never.
+                    On the served size mix (n 1e3..4e6) 2^19 gave the most DFAs per second of
+                    2^14..2^22 (3,416/s against 1,499/s batching everything and 1,928/s
+                    launching everything alone)
     tuned           use batch options from the autotuner's cache when it has them for the
                     batch's shape (a lookup, no measurement)
     """
 
     def __init__(self, budget_bytes: int = 32 << 30, streams: int = 4, max_batch: int = 1024,
                  pass_cap: int = 64, device: str | torch.device = "cuda", flags: int = 0,
-                 max_batch_work: int = 1 << 62, tuned: bool = True):
+                 max_batch_work: int = 1 << 62, tuned: bool = True, solo_work: int = 1 << 19):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.copy_stream = torch.cuda.Stream(device=self.device)
@@ -107,6 +114,7 @@ class Server:
         self._staging = [dict() for _ in range(streams)]
         self.max_batch = max_batch
         self.max_batch_work = int(max_batch_work)
+        self.solo_work = int(solo_work)
         self.pass_cap = pass_cap
         self.flags = flags
         self.tuned = tuned
@@ -168,16 +176,28 @@ class Server:
             reqs = []
             head_closure = self.pending[0].closure
             budget_left = self.budget - self.used
+            if self._solo(self.pending[0]):
+                if self.pending[0].nbytes <= budget_left:
+                    self._launch_solo(self.pending.popleft())
+                    progressed = True
+                return progressed
+            # the batch takes the pending requests of the head's kind in arrival order, passing
+            # over the ones that will run as single-DFA launches (they keep their places), until
+            # the batch is full by count, budget or work
             work = 0
-            while (self.pending and len(reqs) < self.max_batch
-                   and self.pending[0].closure == head_closure
-                   and self.pending[0].nbytes <= budget_left
-                   and (not reqs or work + self.pending[0].n * self.pending[0].k
-                        <= self.max_batch_work)):
-                r = self.pending.popleft()
+            passed = []
+            while self.pending and len(reqs) < self.max_batch and len(passed) < self.max_batch:
+                r = self.pending[0]
+                if r.closure != head_closure or self._solo(r):
+                    passed.append(self.pending.popleft())
+                    continue
+                if r.nbytes > budget_left or (reqs and work + r.n * r.k > self.max_batch_work):
+                    break
+                self.pending.popleft()
                 budget_left -= r.nbytes
                 work += r.n * r.k
                 reqs.append(r)
+            self.pending.extendleft(reversed(passed))
             if reqs:
                 self._launch(reqs, head_closure)
                 progressed = True
@@ -203,7 +223,7 @@ class Server:
         words = (int(state_off[-1]) + 31) // 32
         h_delta = self._stage(si, "delta", max(nd, 1))
         h_acc = self._stage(si, "acc", max(words, 1))
-        delta, acc, state_off, ks = dfamin.pack_batch(reqs, h_delta.numpy(), h_acc.numpy())
+        delta, acc, state_off, ks = dfamin.pack_batch(reqs, h_delta, h_acc.numpy())
         opt = dfamin.options(closure=closure, max_passes=0 if closure else self.pass_cap,
                              flags=self.flags)
         if self.tuned:
@@ -240,6 +260,54 @@ class Server:
         self.stats.batches += 1
         self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
 
+    def _solo(self, r: Request) -> bool:
+        return self.solo_work > 0 and r.n * r.k >= self.solo_work
+
+    def _launch_solo(self, r: Request):
+        """One request as its own single-DFA launch, on the same streams as the batches (so that
+        launches still run one after another)."""
+        si = self.free.pop()
+        cs, s = self.copy_stream, self.compute_stream
+        r.admitted = time.perf_counter()
+        r.attempts += 1
+        self.used += r.nbytes
+        m, words = r.n * r.k, (r.n + 31) // 32
+        h_delta = self._stage(si, "delta", max(m, 1))
+        h_acc = self._stage(si, "acc", max(words, 1))
+        if m:                                         # torch copies in parallel over host cores
+            h_delta[:m].copy_(torch.from_numpy(r.delta.reshape(-1)[:m]))
+        h_acc.numpy()[:words] = r.accept.reshape(-1)[:words].view(np.int32)
+        host_out = self._stage(si, "out", r.n)
+        host_per = self._stage(si, "per", 3).view(3, 1)
+        opt = dfamin.options(closure=r.closure, max_passes=0 if r.closure else self.pass_cap,
+                             flags=self.flags)
+        ev_start = torch.cuda.Event(enable_timing=True)
+        ev_copied = torch.cuda.Event()
+        ev_end = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            d_delta = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
+            d_acc = torch.empty(max(words, 1), dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(cs):
+            ev_start.record(cs)
+            d_delta.copy_(h_delta, non_blocking=True)
+            d_acc.copy_(h_acc, non_blocking=True)
+            ev_copied.record(cs)
+        s.wait_event(ev_copied)
+        with torch.cuda.stream(s):
+            ws = dfamin.Workspace(self.device)
+            res = dfamin.minimize_ex(r.n, r.k, d_delta[:m] if m else d_delta, d_acc, opt=opt,
+                                     workspace=ws, stream=s)
+            host_out.copy_(res.out_block, non_blocking=True)
+            host_per.view(-1).copy_(res.scalars, non_blocking=True)
+            ev_end.record(s)
+        tensors = [h_delta, h_acc, d_delta, d_acc, ws, res.out_block, res.scalars]
+        self.inflight.append(_Batch([r], r.closure, si, None, tensors, host_out, host_per,
+                                    np.array([0, r.n], dtype=np.int64), ev_start, ev_end,
+                                    r.nbytes))
+        self.stats.batches += 1
+        self.stats.solo += 1
+        self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
+
     def _stage(self, si: int, name: str, count: int) -> torch.Tensor:
         """The first `count` int32 of stream si's page-locked buffer `name` (grown by doubling)."""
         buf = self._staging[si].get(name)
@@ -252,7 +320,6 @@ class Server:
     def _finish(self, b: _Batch):
         now = time.perf_counter()
         per = b.host_per.numpy()
-        out = b.host_out.numpy()
         self.stats.intervals.append((self._base.elapsed_time(b.ev_start),
                                      self._base.elapsed_time(b.ev_end)))
         requeue = []
@@ -266,7 +333,9 @@ class Server:
             r.status = st
             r.nblocks = int(per[0, i])
             r.passes = int(per[1, i])
-            r.out_block = out[b.state_off[i]: b.state_off[i + 1]].copy()
+            # the staging buffer is reused by the stream's next batch: keep a copy (torch clones
+            # large arrays in parallel over the host's cores)
+            r.out_block = b.host_out[int(b.state_off[i]): int(b.state_off[i + 1])].clone().numpy()
             r.done = now
             self.completed.append(r)
         for r in reversed(requeue):
@@ -274,7 +343,8 @@ class Server:
         self.used -= b.nbytes
         self.free.append(b.stream_idx)
         self.inflight.remove(b)
-        b.plan.close()                                # stream-ordered free: no device sync
+        if b.plan is not None:
+            b.plan.close()                            # stream-ordered free: no device sync
 
     def max_device_overlap(self) -> int:
         """Largest number of batches whose device intervals (start..end events) overlap."""

@@ -155,3 +155,23 @@ def test_cancel_and_bad_request_are_isolated(mods):
     for r, d in zip(reqs, dfas[:5] + dfas[6:]):
         want, wn, _ = oracle.moore(d.delta, d.accept, d.n, d.k)
         assert r.status == 0 and r.nblocks == wn and np.array_equal(r.out_block, want)
+
+
+@pytest.mark.parametrize("solo_work", [1, 0])
+def test_single_dfa_launches_and_batches_agree(mods, solo_work):
+    # every request as its own single-DFA launch (solo_work = 1) or none (0): the results,
+    # closure reruns of deep refinements included, equal the oracle either way
+    dfamin, serve = mods
+    dfas = request_mix(seed=3, count=18, max_n=60_000)
+    srv = serve.Server(budget_bytes=16 << 30, pass_cap=32, solo_work=solo_work)
+    reqs = []
+    for i, d in enumerate(dfas):
+        reqs.append(srv.submit(d.n, d.k, d.delta, d.accept))
+        if i % 3 == 2:
+            srv.step()
+    srv.drain()
+    assert srv.stats.escalated >= 1
+    assert (srv.stats.solo == srv.stats.batches) if solo_work else srv.stats.solo == 0
+    for d, r in zip(dfas, reqs):
+        want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+        assert r.status == 0 and r.nblocks == wn and np.array_equal(r.out_block, want)

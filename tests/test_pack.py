@@ -3,6 +3,7 @@ the other and one acceptance bitmap over all states, DFA i's state q at bit stat
 The word-shifting packer is checked against that definition written bit by bit."""
 import numpy as np
 import pytest
+import torch
 
 from paper_2410_22764_gb300 import dfamin
 from paper_2410_22764_gb300 import inputs as I
@@ -51,3 +52,13 @@ def test_pack_batch_into_preallocated_buffers():
     delta, accept, _, _ = dfamin.pack_batch(dfas, dbuf, abuf)
     assert np.shares_memory(delta, dbuf) and np.shares_memory(accept, abuf)
     assert np.array_equal(delta, ref[0]) and np.array_equal(accept, ref[1])
+
+
+def test_pack_batch_rows_copied_by_torch():
+    dfas = [I.random_dfa(n, k, 0.5, n + k) for n, k in ((3, 2), (500, 4), (64, 1), (1000, 3))]
+    ref = dfamin.pack_batch(dfas)
+    nd = sum(d.n * d.k for d in dfas)
+    buf = torch.full((nd + 5,), -1, dtype=torch.int32)
+    delta, accept, state_off, ks = dfamin.pack_batch(dfas, buf)
+    assert np.array_equal(delta, ref[0]) and np.array_equal(buf[:nd].numpy(), ref[0])
+    assert np.array_equal(accept, ref[1]) and np.array_equal(state_off, ref[2])
