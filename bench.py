@@ -322,7 +322,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="config2",
                     choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve",
-                             "table2", "minimal"])
+                             "table2", "minimal", "trace2"])
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-pool", type=int, default=256,
                     help="distinct DFAs the served stream draws its requests from")

@@ -500,8 +500,51 @@ def run_minimal(args):
           {"minimal": rows})
 
 
+PHASES = {0: "start", 1: "validate", 2: "partition", 3: "closure level", 4: "leaders",
+          5: "members", 6: "moves", 7: "count", 8: "canonical"}
+
+
+def run_trace2(args):
+    """Per-phase device times of the bench workload (n = 10^7, k = 4) with DFAMIN_FLAG_TRACE,
+    for the default choice of rounds, every round full and every round incremental, beside the
+    median of untraced launches of each (CUDA events, L2 flushed between launches)."""
+    d = bench.make_workload(bench.BASE_M)
+    dd, aa = dfamin.to_device(d.delta, d.accept)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")     # > L2
+    out = torch.empty(d.n, dtype=torch.int32, device="cuda")
+    sc = torch.zeros(3, dtype=torch.int32, device="cuda")
+    res, labels = {}, []
+    for name, fl in (("default", 0), ("full", dfamin.FLAG_FULL_ROUNDS),
+                     ("incremental", dfamin.FLAG_INCREMENTAL_ROUNDS)):
+        opt = dfamin.options(flags=fl)
+        ws = dfamin.Workspace()
+        ms = _time_steps(lambda: dfamin.minimize_ex(d.n, d.k, dd, aa, opt=opt, workspace=ws,
+                                                    out_block=out, scalars=sc),
+                         30, 3, flush)
+        labels.append(out.cpu().numpy())
+        topt = dfamin.options(flags=fl | dfamin.FLAG_TRACE)
+        tws = dfamin.Workspace()
+        for _ in range(2):
+            dfamin.minimize_ex(d.n, d.k, dd, aa, opt=topt, workspace=tws)
+        torch.cuda.synchronize()
+        tr = dfamin.read_trace(tws, d.n, d.k, topt)
+        phases, prev = [], tr[0][2]
+        for p_, ph, t in tr[1:]:
+            phases.append([int(p_), PHASES.get(int(ph), str(ph)), round((t - prev) / 1e3, 1)])
+            prev = t
+        res[name] = {"median_ms": statistics.median(ms), "scalars": sc.cpu().tolist(),
+                     "phases_us": phases}
+    same = all(np.array_equal(labels[0], x) for x in labels[1:])
+    _line("per-phase trace of the inflated random DFA n=10^7 k=4 (default, full and incremental "
+          "rounds)", res["default"]["median_ms"], "ms", res["default"]["median_ms"], 30, 3,
+          {"trace": res, "labels_equal": same}, higher=False)
+
+
 def run(args):
     torch.cuda.set_device(bench.dist_env()[2])
+    if args.workload == "trace2":
+        run_trace2(args)
+        return 0
     if args.workload == "random1k":
         run_random1k(args)
     elif args.workload == "path":
