@@ -500,10 +500,6 @@ def run_minimal(args):
           {"minimal": rows})
 
 
-PHASES = {0: "start", 1: "validate", 2: "partition", 3: "closure level", 4: "leaders",
-          5: "members", 6: "moves", 7: "count", 8: "canonical"}
-
-
 def run_trace2(args):
     """Per-phase device times of the bench workload (n = 10^7, k = 4) with DFAMIN_FLAG_TRACE,
     for the default choice of rounds, every round full and every round incremental, beside the
@@ -530,7 +526,7 @@ def run_trace2(args):
         tr = dfamin.read_trace(tws, d.n, d.k, topt)
         phases, prev = [], tr[0][2]
         for p_, ph, t in tr[1:]:
-            phases.append([int(p_), PHASES.get(int(ph), str(ph)), round((t - prev) / 1e3, 1)])
+            phases.append([int(p_), str(ph), round((t - prev) / 1e3, 1)])
             prev = t
         res[name] = {"median_ms": statistics.median(ms), "scalars": sc.cpu().tolist(),
                      "phases_us": phases}
