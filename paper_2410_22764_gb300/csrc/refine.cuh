@@ -95,6 +95,7 @@ struct Job {
     int32_t* cl_letter;                  // [k] letters with closure columns (compacted)
     int32_t* nonid;                      // [k] 1 if letter is not the identity
     unsigned long long* table;           // [cap] group table: (min state << 32) | representative
+                                         // (runtime width) or | old block id (compile-time)
     int32_t* sig;                        // [n * sig_stride] signature rows
     int32_t sig_stride;                  // ints per row, multiple of 4, >= ncols + 1
     int32_t* lst_s;                      // [n] changed states, per-CTA segments
@@ -364,19 +365,22 @@ static __device__ int cta_min(int v)
 }
 
 // ------------------------------------------------------------------------------------------
-// Signature rows.  sig[s*SS .. s*SS+SS) holds the full signature of s in the current round,
-// T(s) = (block[s], block[succ(s,0)], ..., block[succ(s,K-1)]), padded with zeros to SS ints
-// (SS a multiple of 4, so rows are read and written as int4).  A leader writes its row in phase
-// A; a member compares its own signature with its leader's row (one sector instead of
-// regathering the leader's successors); a member that differs publishes its row before it
-// enters the hash table, so the table can verify equality against any slot holder's row.
+// Signature rows.  The signature of s in the current round is T(s) = (block[s],
+// block[succ(s,0)], ..., block[succ(s,K-1)]).  The runtime-width rows hold all of it,
+// [head, b_0 ..], padded with zeros to a multiple of 4 ints (read and written as int4); the
+// compile-time-width rows hold only the successors' ids (the head is known to every reader, see
+// RowOf).  A leader writes its row in phase A; a member compares its own signature with its
+// leader's row (one sector instead of regathering the leader's successors); a member that
+// differs publishes its row before it enters the hash table, so the table can verify equality
+// against the row of the state a slot names.
 // ------------------------------------------------------------------------------------------
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr uint32_t kFail = 0xffffffffu;
-// A group-table slot holds (smallest member << 32) | representative.  The representative is the
-// state that claimed the slot; its row is the one members compare against, and it never
-// changes during a round, so only claimers publish rows.  atomicMin on the whole word lowers
-// the smallest member and keeps the representative (every member passes the same low half).
+// A runtime-width group-table slot holds (smallest member << 32) | representative.  The
+// representative is the state that claimed the slot; its row is the one members compare
+// against, and it never changes during a round, so only claimers publish rows.  atomicMin on the
+// whole word lowers the smallest member and keeps the representative (every member passes the
+// same low half).  Compile-time-width slots hold the old block id instead (see insert_row).
 constexpr unsigned long long kEmptySlot = ~0ull;
 
 static __device__ __forceinline__ unsigned long long slot_word(int min_state, int rep)
