@@ -56,13 +56,7 @@ constexpr int kTeamThreads = DFAMIN_TEAM_THREADS;
 constexpr int kMaxCtas = 8192;            // capacity of the per-CTA count array
 constexpr int64_t kBarrierTimeoutNs = 4000000000ll;        // 4 s per CTA barrier
 constexpr int kSmallMaxStates = 8192;     // largest n for the shared-memory kernel
-constexpr int kPatMaxK = 8;
-#ifndef DFAMIN_RB_UNROLL
-#define DFAMIN_RB_UNROLL 4                // dense round's read-back: states per thread per step
-#endif
-#ifndef DFAMIN_MASK_U34
-#define DFAMIN_MASK_U34 1                 // masked leaders per thread at a time for k = 3, 4
-#endif               // round 1 from acceptance bits for k <= kPatMaxK
+constexpr int kPatMaxK = 8;               // round 1 from acceptance bits for k <= kPatMaxK
 constexpr int kPatMax = 1 << (kPatMaxK + 1);
 
 // ------------------------------------------------------------------------------------------
@@ -916,7 +910,7 @@ static __device__ void phase_leaders(const Job& J, int rank, int T, int nlead, i
                 // successors and the gathers of the marked letters).  A row without marks that
                 // needs none is left as it is.
                 constexpr int NB = RowOf<KC>::NB;
-                constexpr int U = KC <= 2 ? 2 : (KC <= 4 ? DFAMIN_MASK_U34 : 1);
+                constexpr int U = KC <= 2 ? 2 : 1;
                 for (int i0 = gid; i0 < nlead; i0 += U * stride) {
                     int sv[U];
 #pragma unroll
@@ -1726,32 +1720,31 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     // every group's smallest state leads it and lists its table word for reset
                     if (threadIdx.x == 0) s_rst = 0;
                     __syncthreads();
-                    // RBU states per thread per step; the next step's codes are in flight
-                    constexpr int RBU = DFAMIN_RB_UNROLL;
-                    uint32_t ncv[RBU];
+                    // four states per thread per step; the next step's codes are in flight
+                    uint32_t ncv[4];
 #pragma unroll
-                    for (int u = 0; u < RBU; ++u) {
+                    for (int u = 0; u < 4; ++u) {
                         const int q = c0 + u * (int)blockDim.x + (int)threadIdx.x;
                         ncv[u] = q < c1 ? __ldcs(&J.lst_slot[q]) : 0u;
                     }
-                    for (int b = c0; b < c1; b += RBU * (int)blockDim.x) {
-                        int qv[RBU], mv[RBU];
-                        uint32_t cv[RBU];
+                    for (int b = c0; b < c1; b += 4 * (int)blockDim.x) {
+                        int qv[4], mv[4];
+                        uint32_t cv[4];
 #pragma unroll
-                        for (int u = 0; u < RBU; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             qv[u] = b + u * (int)blockDim.x + (int)threadIdx.x;
                             cv[u] = ncv[u];
                         }
 #pragma unroll
-                        for (int u = 0; u < RBU; ++u)
+                        for (int u = 0; u < 4; ++u)
                             mv[u] = qv[u] < c1 ? (int)__ldcg(&dtab[cv[u]]) : -1;
 #pragma unroll
-                        for (int u = 0; u < RBU; ++u) {
-                            const int q = qv[u] + RBU * (int)blockDim.x;
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = qv[u] + 4 * (int)blockDim.x;
                             ncv[u] = q < c1 ? __ldcs(&J.lst_slot[q]) : 0u;
                         }
 #pragma unroll
-                        for (int u = 0; u < RBU; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             if (qv[u] < c1) J.block[qv[u]] = mv[u];
                             append_pair(J, c0, &s_rst, qv[u] < c1 && mv[u] == qv[u], qv[u],
                                         cv[u] >> 1);
