@@ -152,6 +152,42 @@ def _graph_of(fn, stream):
     return g
 
 
+def _oracle_member(task):
+    """Pool task (spawn-started worker): regenerate one batch member from its draws with the
+    seeded generator and run the CPU oracle (Hopcroft) on it; returns the oracle's seconds and
+    block count (the generation is not timed)."""
+    n, k, p, seed = task
+    import oracle
+    delta, acc, _, _ = I.random_batch([n], [k], [p], [seed], threads=1)
+    t0 = time.perf_counter()
+    _, nb = oracle.hopcroft(delta, acc, n, k)
+    return time.perf_counter() - t0, int(nb)
+
+
+def _cpu_baseline_batch(ns, ks, ps, seeds, stride, nblocks):
+    """The CPU oracle as it stands (Hopcroft, one DFA per task) over all host cores on every
+    `stride`-th member of the batch; value = DFAs per second on those cores, from the sum of the
+    per-DFA oracle times divided by the cores (the pool's own overhead not counted)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    idx = np.arange(0, ns.size, stride)
+    tasks = [(int(ns[i]), int(ks[i]), float(ps[i]), int(seeds[i])) for i in idx]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        out = pool.map(_oracle_member, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    cpu_s = sum(t for t, _ in out)
+    assert all(nb == int(nblocks[i]) for (_, nb), i in zip(out, idx))
+    trans = int(np.sum(ns[idx] * ks[idx].astype(np.int64)))
+    return {"value": len(tasks) / (cpu_s / cores), "unit": "DFAs/s", "cores": cores,
+            "host_cores": cores, "kind": "oracle", "oracle_cpu_s": cpu_s, "wall_s": wall,
+            "transitions_per_s": trans / (cpu_s / cores),
+            "sample": f"every {stride}th of the 4,096 DFAs ({len(tasks)} DFAs, {trans} "
+                      "transitions), Hopcroft per DFA in a process pool over all host cores; "
+                      "value = DFAs / (sum of per-DFA oracle seconds / cores); block counts "
+                      "equal the GPU's"}
+
+
 def run_batch(args, kind):
     """One persistent launch per batch, replayed from a CUDA graph, with the options the
     autotuner picks (timed candidates, cached per GPU and shape bucket), against the default
@@ -223,6 +259,11 @@ def run_batch(args, kind):
         pms, pout, psc = _per_dfa_launches(delta, acc, state_off, ks, 2)
         assert np.array_equal(pout, ref[0]) and np.array_equal(psc[:, 0], p[0])
         extra.update({"per_dfa_launches_ms": pms, "batched_speedup": pms / ms})
+    if world == 1 and not getattr(args, "no_cpu_baseline", False):
+        nb_by_index = np.zeros(ns.size, dtype=np.int64)
+        nb_by_index[mine] = p[0]
+        extra["cpu_baseline"] = _cpu_baseline_batch(ns, ks_all, ps, seeds,
+                                                    1 if kind == "4b" else 16, nb_by_index)
     desc = ("4,096 random DFAs, n log-uniform 100..1e6, k 2..26, p 0.1..0.9, seed 1" +
             (", n capped so that sum n*k = 2e8" if kind == "4b" else ", as drawn") +
             "; one persistent launch replayed from a CUDA graph with autotuned options")
