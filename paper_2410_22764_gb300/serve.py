@@ -61,12 +61,13 @@ class _Batch:
     stream_idx: int
     plan: object
     tensors: list
-    host_out: torch.Tensor
+    host_out: torch.Tensor | None      # page-locked labels, or None (labels kept on the device)
     host_per: torch.Tensor
     state_off: np.ndarray
     ev_start: torch.cuda.Event
     ev_end: torch.cuda.Event
     nbytes: int
+    dev_out: torch.Tensor | None = None  # the launch's labels on the device
 
 
 @dataclass
@@ -92,6 +93,10 @@ class Server:
     solo_work       transitions (n*k) from which a request runs as its own single-DFA launch
                     (`dfamin_minimize_ex`, the whole GPU for one DFA) instead of joining a
                     batch, in which it would get one team and hold the batch up; 0 = never.
+    results_on_device  keep every finished request's labels in device memory (a CUDA int32
+                    tensor in ``Request.out_block``, owned by the caller and outside the budget)
+                    instead of copying them to the host; only the per-request scalars (block
+                    count, passes, status) come back
                     On the served size mix (n 1e3..4e6) 2^19 gave the most DFAs per second of
                     2^14..2^22 (3,416/s against 1,499/s batching everything and 1,928/s
                     launching everything alone)
@@ -101,7 +106,8 @@ class Server:
 
     def __init__(self, budget_bytes: int = 32 << 30, streams: int = 4, max_batch: int = 1024,
                  pass_cap: int = 64, device: str | torch.device = "cuda", flags: int = 0,
-                 max_batch_work: int = 1 << 62, tuned: bool = True, solo_work: int = 1 << 19):
+                 max_batch_work: int = 1 << 62, tuned: bool = True, solo_work: int = 1 << 19,
+                 results_on_device: bool = False):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.copy_stream = torch.cuda.Stream(device=self.device)
@@ -115,6 +121,7 @@ class Server:
         self.max_batch = max_batch
         self.max_batch_work = int(max_batch_work)
         self.solo_work = int(solo_work)
+        self.results_on_device = bool(results_on_device)
         self.pass_cap = pass_cap
         self.flags = flags
         self.tuned = tuned
@@ -232,7 +239,7 @@ class Server:
                 opt.smem_states, opt.team_states, opt.ctas = t.smem_states, t.team_states, t.ctas
                 opt.flags |= t.flags
         plan = dfamin.BatchPlan(state_off, ks, opt)
-        host_out = self._stage(si, "out", plan.states)
+        host_out = None if self.results_on_device else self._stage(si, "out", plan.states)
         host_per = self._stage(si, "per", 3 * plan.count).view(3, plan.count)
         ev_start = torch.cuda.Event(enable_timing=True)
         ev_copied = torch.cuda.Event()
@@ -251,12 +258,13 @@ class Server:
         with torch.cuda.stream(s):
             ws = dfamin.Workspace(self.device)
             out, per = plan.run(d_delta, d_acc, workspace=ws, stream=s)
-            host_out.copy_(out, non_blocking=True)
+            if host_out is not None:
+                host_out.copy_(out, non_blocking=True)
             host_per.copy_(per, non_blocking=True)
             ev_end.record(s)
         tensors = [h_delta, h_acc, d_delta, d_acc, ws, out, per]
         self.inflight.append(_Batch(reqs, closure, si, plan, tensors, host_out, host_per,
-                                    state_off, ev_start, ev_end, nbytes))
+                                    state_off, ev_start, ev_end, nbytes, dev_out=out))
         self.stats.batches += 1
         self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
 
@@ -277,7 +285,7 @@ class Server:
         if m:                                         # torch copies in parallel over host cores
             h_delta[:m].copy_(torch.from_numpy(r.delta.reshape(-1)[:m]))
         h_acc.numpy()[:words] = r.accept.reshape(-1)[:words].view(np.int32)
-        host_out = self._stage(si, "out", r.n)
+        host_out = None if self.results_on_device else self._stage(si, "out", r.n)
         host_per = self._stage(si, "per", 3).view(3, 1)
         opt = dfamin.options(closure=r.closure, max_passes=0 if r.closure else self.pass_cap,
                              flags=self.flags)
@@ -297,13 +305,14 @@ class Server:
             ws = dfamin.Workspace(self.device)
             res = dfamin.minimize_ex(r.n, r.k, d_delta[:m] if m else d_delta, d_acc, opt=opt,
                                      workspace=ws, stream=s)
-            host_out.copy_(res.out_block, non_blocking=True)
+            if host_out is not None:
+                host_out.copy_(res.out_block, non_blocking=True)
             host_per.view(-1).copy_(res.scalars, non_blocking=True)
             ev_end.record(s)
         tensors = [h_delta, h_acc, d_delta, d_acc, ws, res.out_block, res.scalars]
         self.inflight.append(_Batch([r], r.closure, si, None, tensors, host_out, host_per,
                                     np.array([0, r.n], dtype=np.int64), ev_start, ev_end,
-                                    r.nbytes))
+                                    r.nbytes, dev_out=res.out_block))
         self.stats.batches += 1
         self.stats.solo += 1
         self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
@@ -335,7 +344,14 @@ class Server:
             r.passes = int(per[1, i])
             # the staging buffer is reused by the stream's next batch: keep a copy (torch clones
             # large arrays in parallel over the host's cores)
-            r.out_block = b.host_out[int(b.state_off[i]): int(b.state_off[i + 1])].clone().numpy()
+            lo, hi = int(b.state_off[i]), int(b.state_off[i + 1])
+            if b.host_out is None:
+                # on the device: a batch's labels share one tensor, so each request gets its
+                # own copy (a single-DFA launch's tensor is the request's already)
+                r.out_block = b.dev_out if len(b.reqs) == 1 and b.plan is None \
+                    else b.dev_out[lo:hi].clone()
+            else:
+                r.out_block = b.host_out[lo:hi].clone().numpy()
             r.done = now
             self.completed.append(r)
         for r in reversed(requeue):

@@ -175,3 +175,20 @@ def test_single_dfa_launches_and_batches_agree(mods, solo_work):
     for d, r in zip(dfas, reqs):
         want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
         assert r.status == 0 and r.nblocks == wn and np.array_equal(r.out_block, want)
+
+
+def test_results_kept_on_the_device(mods):
+    # labels stay in device memory (single-DFA launches and batch members alike) and equal
+    # the oracle's
+    dfamin, serve = mods
+    dfas = request_mix(seed=4, count=12, max_n=80_000) + [I.random_dfa(200_000, 4, 0.5, 9)]
+    srv = serve.Server(budget_bytes=16 << 30, pass_cap=32, solo_work=1 << 19,
+                       results_on_device=True)
+    reqs = [srv.submit(d.n, d.k, d.delta, d.accept) for d in dfas]
+    srv.drain()
+    assert srv.stats.solo >= 1 and srv.stats.batches > srv.stats.solo
+    for d, r in zip(dfas, reqs):
+        assert isinstance(r.out_block, torch.Tensor) and r.out_block.is_cuda
+        want, wn = oracle.hopcroft(d.delta, d.accept, d.n, d.k)
+        assert r.status == 0 and r.nblocks == wn
+        assert np.array_equal(r.out_block.cpu().numpy(), want)
