@@ -3,7 +3,7 @@
 n = 10,000,000, permuted ids, seed 1) on one GB300 per rank and print one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config2|random1k|path|batch4b|batch4a|serve|table2|minimal]
+                  [--workload inflated10m|random1k|path|batch200m|batch6g|serve|table2|minimal|trace2]
 
 A step is one full minimization (every refinement round until the partition is stable,
 plus the canonical renumbering) of the DFA already resident in HBM.  ``value`` is edge visits
@@ -320,8 +320,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="config2",
-                    choices=["config2", "random1k", "path", "batch4b", "batch4a", "serve",
+    ap.add_argument("--workload", default="inflated10m",
+                    choices=["inflated10m", "random1k", "path", "batch200m", "batch6g", "serve",
                              "table2", "minimal", "trace2"])
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-pool", type=int, default=256,
@@ -339,7 +339,7 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload != "config2":
+    if args.workload != "inflated10m":
         import bench_workloads
         return bench_workloads.run(args)
 
@@ -446,7 +446,7 @@ def main():
     alg_bytes = passes * 4 * n * (k + 2)           # per launch: passes x 4n(k+2)
     kernel_ms = statistics.mean(step_ms)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = profiled_traffic("team_kernel", "config2")
+    traffic = profiled_traffic("team_kernel", "inflated10m")
     gather = gather_roofline(n, k, passes, kernel_ms)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],

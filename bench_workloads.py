@@ -1,11 +1,11 @@
 """Measurement of the other workloads (one JSON line each), selected by
-``python bench.py --workload random1k|path|batch4b|batch4a|serve|table2``.
+``python bench.py --workload random1k|path|batch200m|batch6g|serve|table2|minimal|trace2``.
 
 * random1k  random DFA n = 1,000, k = 2 (one CTA in shared memory): ms per minimization.
 * path      deep-refinement path n = 2^20, k = 2: plain rounds (534,348) against the closure.
-* batch4b   4,096 random DFAs (n log-uniform 100..10^6 capped so that sum n*k = 2e8, k in 2..26,
+* batch200m 4,096 random DFAs (n log-uniform 100..10^6 capped so that sum n*k = 2e8, k in 2..26,
             p in 0.1..0.9): one batched launch against one launch per DFA.
-* batch4a   the same 4,096 draws uncapped (~6.5e9 transitions): one batched launch.
+* batch6g   the same 4,096 draws uncapped (~6.5e9 transitions): one batched launch.
 * serve     Poisson request stream through the continuous-batching server at
             0.5 / 0.8 / 0.95 of its saturated throughput: p50 / p99 latency and DFAs/s.
 * minimal   the minimal DFA of the bench workload (n = 10^7, q0 = 0): reachability, refinement
@@ -202,7 +202,7 @@ def run_batch(args, kind):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     ns, ks_all, ps, seeds = I.batch_sizes(4096, 1)
-    if kind == "4b":
+    if kind == "capped":
         cap = I.batch_cap_for_transitions(4096, 1, 200_000_000)
         ns, ks_all, ps, seeds = I.batch_sizes(4096, 1, n_cap=cap)
     mine = multi.shard_batch(ns, ks_all, world)[rank]
@@ -213,7 +213,7 @@ def run_batch(args, kind):
     t0 = time.perf_counter()
     tuned_opt, timings = autotune.tune_batch(state_off, ks, dd, aa)
     tune_s = time.perf_counter() - t0
-    steps = max(3, min(args.steps, 10 if kind == "4b" else 5))
+    steps = max(3, min(args.steps, 10 if kind == "capped" else 5))
     warm = max(3, args.warmup)
     side = torch.cuda.Stream()
     res, ref = {}, None
@@ -255,7 +255,7 @@ def run_batch(args, kind):
         extra.update({"n_gpus": world, "scaling": "strong",
                       "parallelism": f"batch sharded over {world} ranks (size-balanced)",
                       "rank0_dfas": int(mine.size)})
-    if kind == "4b" and world == 1:
+    if kind == "capped" and world == 1:
         pms, pout, psc = _per_dfa_launches(delta, acc, state_off, ks, 2)
         assert np.array_equal(pout, ref[0]) and np.array_equal(psc[:, 0], p[0])
         extra.update({"per_dfa_launches_ms": pms, "batched_speedup": pms / ms})
@@ -263,9 +263,9 @@ def run_batch(args, kind):
         nb_by_index = np.zeros(ns.size, dtype=np.int64)
         nb_by_index[mine] = p[0]
         extra["cpu_baseline"] = _cpu_baseline_batch(ns, ks_all, ps, seeds,
-                                                    1 if kind == "4b" else 16, nb_by_index)
+                                                    1 if kind == "capped" else 16, nb_by_index)
     desc = ("4,096 random DFAs, n log-uniform 100..1e6, k 2..26, p 0.1..0.9, seed 1" +
-            (", n capped so that sum n*k = 2e8" if kind == "4b" else ", as drawn") +
+            (", n capped so that sum n*k = 2e8" if kind == "capped" else ", as drawn") +
             "; one persistent launch replayed from a CUDA graph with autotuned options")
     if rank == 0:
         _line(desc, visits / (ms / 1e3), "edge-visits/s", ms, steps, warm, extra)
@@ -586,8 +586,8 @@ def run(args):
         run_random1k(args)
     elif args.workload == "path":
         run_path(args)
-    elif args.workload in ("batch4b", "batch4a"):
-        run_batch(args, args.workload[-2:])
+    elif args.workload in ("batch200m", "batch6g"):
+        run_batch(args, "capped" if args.workload == "batch200m" else "drawn")
     elif args.workload == "serve":
         run_serve(args)
     elif args.workload == "table2":

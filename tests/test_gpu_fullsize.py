@@ -68,13 +68,13 @@ def pool():
 
 def _draws(kind):
     ns, ks, ps, seeds = I.batch_sizes(4096, 1)
-    if kind == "4b":
+    if kind == "capped":
         cap = I.batch_cap_for_transitions(4096, 1, 200_000_000)
         ns, ks, ps, seeds = I.batch_sizes(4096, 1, n_cap=cap)
     return ns, ks, ps, seeds
 
 
-@pytest.mark.parametrize("kind", ["4b", "4a"])
+@pytest.mark.parametrize("kind", ["capped", "drawn"])
 def test_batch_4096_every_member(dm, pool, kind):
     # every member of the batch against the oracle, one DFA per host core (Moore up to 300,000
     # states, with its pass count; Hopcroft above, compared through a digest of its labels)

@@ -58,7 +58,7 @@ def test_large_alphabet(dm, n):
     check(dm, I.random_dfa(n, 26, 0.3, 5))
 
 
-def test_config1_against_three_oracles(dm):
+def test_random1k_against_three_oracles(dm):
     # random complete DFA, n = 1000, k = 2, p = 0.5, seed 1
     d = I.random_dfa(1000, 2, 0.5, 1)
     got, gn, gp, st = run(dm, d)
