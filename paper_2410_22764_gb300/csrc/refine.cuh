@@ -33,6 +33,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 #include "dfamin.h"
 
@@ -1583,6 +1584,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
     if constexpr (KC > 0 && KC <= kPatMaxK) {
         if (J.pat_rev && !closure && J.algo == DFAMIN_ALG_SIGNATURE) {
             constexpr int NP = 1 << (KC + 1);
+            using PatT = typename std::conditional<(KC <= 7), uint8_t, int32_t>::type;
             __shared__ int s_pat[NP];
             for (int i = threadIdx.x; i < NP; i += blockDim.x) s_pat[i] = 0x7fffffff;
             __syncthreads();
@@ -1605,8 +1607,9 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                     if ((unsigned)r[c] >= (unsigned)n) bad = true;
                     else pat |= (is_accepting(J, r[c]) ? 1 : 0) << (c + 1);
                 }
-                J.block[q] = pat;                     // the pattern, until the ids are known
-                J.naive_new[q] = pat;                 // kept for a dense round 2
+                // the pattern, until the ids are known (one byte a state for k <= 7: the dense
+                // round 2 gathers it from an array a quarter the size)
+                reinterpret_cast<PatT*>(J.naive_new)[q] = (PatT)pat;
                 if (q < s_pat[pat]) atomicMin(&s_pat[pat], q);
             }
             if (bad) set_status(J.ctrl, DFAMIN_EINVAL);
@@ -1642,7 +1645,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             }
             if (!dense_next) {
                 for (int q = c0 + threadIdx.x; q < c1; q += blockDim.x)
-                    J.block[q] = n - s_pat[J.block[q]];
+                    J.block[q] = n - s_pat[reinterpret_cast<const PatT*>(J.naive_new)[q]];
                 if (rank == 0 && threadIdx.x == 0) {
                     int m = 0;
                     for (int i = 0; i < NP; ++i)
@@ -1667,7 +1670,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
             if constexpr (CB <= 26) {
                 if (dense_next) {
                     uint32_t* dtab = reinterpret_cast<uint32_t*>(J.table);
-                    const int32_t* pidx = J.naive_new;
+                    const PatT* pidx = reinterpret_cast<const PatT*>(J.naive_new);
                     if (threadIdx.x == 0) s_claims = 0;
                     __syncthreads();
                     int mine = 0;
@@ -1697,7 +1700,7 @@ static __device__ void team_minimize(const Job& J, int rank, int T, TeamSync& ts
                             code[u] = (uint32_t)__ldcs(&pidx[qv[u]]) & 1u;   // acceptance of q
 #pragma unroll
                             for (int c = 0; c < KC; ++c)
-                                code[u] |= (uint32_t)ld_blk(&pidx[r[c]]) << (1 + c * PB);
+                                code[u] |= (uint32_t)__ldcg(&pidx[r[c]]) << (1 + c * PB);
                         }
                         uint32_t old[2] = {0u, 0u};
 #pragma unroll
