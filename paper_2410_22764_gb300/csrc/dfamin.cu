@@ -16,8 +16,18 @@
 
 namespace dfamin_dev {
 
+// CTA shape of the single-DFA team kernel: 512 threads, two CTAs (64 registers a thread) per SM
+// for k <= 5 and the runtime width; 256 threads, three CTAs (80 registers) for k = 6..8.  With
+// half as many CTAs as 256-thread ones the team's barriers gather half the arrivals (measured:
+// plain path rounds 17.6 -> 16.2 us, the inflated n = 10^7 DFA 0.940 -> 0.929 ms).
 template <int KC>
-__global__ void __launch_bounds__(kTeamThreads, (KC >= 6 ? DFAMIN_TEAM_MIN_CTAS - 1 : DFAMIN_TEAM_MIN_CTAS)) team_kernel(Job J)
+struct TeamShape {
+    static constexpr int threads = (KC >= 6) ? 256 : 512;
+    static constexpr int min_ctas = (KC >= 6) ? 3 : 2;
+};
+
+template <int KC>
+__global__ void __launch_bounds__(TeamShape<KC>::threads, TeamShape<KC>::min_ctas) team_kernel(Job J)
 {
     TeamSync ts{&J.ctrl->bar, &J.ctrl->status, (unsigned long long)gridDim.x, 0ull, J.timeout_ns};
     team_minimize<KC>(J, blockIdx.x, gridDim.x, ts);
@@ -154,29 +164,31 @@ Layout make_layout(int32_t n, int32_t k, const dfamin_options& o)
 // Alphabet sizes with a compile-time kernel; every other size, and every closure run, uses
 // the runtime-width kernel team_kernel<0>.  *smem receives the kernel's dynamic shared memory.
 template <int KC>
-const void* team_entry(size_t* smem)
+const void* team_entry(size_t* smem, int* threads)
 {
     *smem = sizeof(typename CacheOf<KC>::type);
+    *threads = TeamShape<KC>::threads;
     return (const void*)team_kernel<KC>;
 }
 
-const void* team_kernel_for(int k, bool closure, const int32_t* delta, size_t* smem)
+const void* team_kernel_for(int k, bool closure, const int32_t* delta, size_t* smem, int* threads)
 {
     const bool aligned = ((uintptr_t)delta & 15u) == 0;
     if (!closure && aligned) {
         switch (k) {
-        case 1: return team_entry<1>(smem);
-        case 2: return team_entry<2>(smem);
-        case 3: return team_entry<3>(smem);
-        case 4: return team_entry<4>(smem);
-        case 5: return team_entry<5>(smem);
-        case 6: return team_entry<6>(smem);
-        case 7: return team_entry<7>(smem);
-        case 8: return team_entry<8>(smem);
+        case 1: return team_entry<1>(smem, threads);
+        case 2: return team_entry<2>(smem, threads);
+        case 3: return team_entry<3>(smem, threads);
+        case 4: return team_entry<4>(smem, threads);
+        case 5: return team_entry<5>(smem, threads);
+        case 6: return team_entry<6>(smem, threads);
+        case 7: return team_entry<7>(smem, threads);
+        case 8: return team_entry<8>(smem, threads);
         default: break;
         }
     }
     *smem = 0;
+    *threads = TeamShape<0>::threads;
     return (const void*)team_kernel<0>;
 }
 
@@ -336,16 +348,17 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
         }
     }
     size_t dsmem = 0;
-    const void* kern = team_kernel_for(k, L.d.levels > 1, delta, &dsmem);
+    int threads = 0;
+    const void* kern = team_kernel_for(k, L.d.levels > 1, delta, &dsmem, &threads);
     int per_sm = 0;
-    st = kernel_ctas_per_sm(dev, kern, kTeamThreads, dsmem, &per_sm);
+    st = kernel_ctas_per_sm(dev, kern, threads, dsmem, &per_sm);
     if (st != DFAMIN_OK) return st;
     int max_ctas = sms * per_sm;
     if (max_ctas > kMaxCtas) max_ctas = kMaxCtas;
     if (max_ctas < 1) return DFAMIN_ECUDA;
     int ctas = o.ctas > 0 ? o.ctas : max_ctas;
     // at least ~2 states per thread per CTA: small DFAs use fewer CTAs (cheaper barriers)
-    const int64_t want = ((int64_t)n + 2 * kTeamThreads - 1) / (2 * kTeamThreads);
+    const int64_t want = ((int64_t)n + 2 * threads - 1) / (2 * threads);
     if (o.ctas == 0 && want < ctas) ctas = (int)(want > 0 ? want : 1);
     if (ctas > max_ctas) ctas = max_ctas;
     // end-to-end: round 1 of a compile-time alphabet reads every row itself (from host memory
@@ -368,7 +381,7 @@ dfamin_status launch_one(int32_t n, int32_t k, const int32_t* delta, const uint3
     st = host_io_copy(io, true, rows_in_kernel, n, k, (int32_t*)delta, out_block, stream);
     if (st != DFAMIN_OK) return st;
     void* args[] = {&J};
-    if (!cuda_ok(cudaLaunchCooperativeKernel(kern, dim3(ctas), dim3(kTeamThreads), args, dsmem,
+    if (!cuda_ok(cudaLaunchCooperativeKernel(kern, dim3(ctas), dim3(threads), args, dsmem,
                                              stream),
                  "team_kernel cooperative launch"))
         return DFAMIN_ECUDA;
