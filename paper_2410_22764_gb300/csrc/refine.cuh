@@ -42,10 +42,10 @@ namespace dfamin_dev {
 
 constexpr int kThreads = 256;             // threads per CTA of the one-CTA kernel
 #ifndef DFAMIN_TEAM_THREADS
-#define DFAMIN_TEAM_THREADS 256           // threads per CTA of the team kernel
-#endif
+#define DFAMIN_TEAM_THREADS 256           // threads per CTA of the batch and reachability teams
+#endif                                    // (the single-DFA team kernel sets its own shape)
 #ifndef DFAMIN_TEAM_MIN_CTAS
-#define DFAMIN_TEAM_MIN_CTAS 4            // team kernel: CTAs per SM the register budget targets
+#define DFAMIN_TEAM_MIN_CTAS 4            // unused by the kernels (kept for builds that set it)
 #endif
 #ifndef DFAMIN_PREFETCH
 #define DFAMIN_PREFETCH 1                 // load the next state's block id and row ahead
